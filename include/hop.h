@@ -1,0 +1,236 @@
+/*
+ * hop.h -- C ABI of the GB300 HOP halo finder (libhop.so).
+ *
+ * HOP (Eisenstein & Hut 1998) as restated in Parallel HOP (Skory, Turk,
+ * Norman & Coil, arXiv:1001.3411, Sec. 2) assigns every particle of a
+ * periodic box to a density-peak group:
+ *   1. the Ndens nearest neighbours of each particle, itself included, give
+ *      an SPH kernel density normalised to the mean particle density;
+ *   2. each particle hops to the densest of its first Nhop neighbours
+ *      (possibly itself), and hops are followed uphill to a peak (a chain);
+ *   3. over the first Nmerge neighbours, the densest pair straddling two
+ *      chains gives their boundary density;
+ *   4. chains merge into groups under delta_outer, delta_saddle, delta_peak.
+ * Sec. 4 ("Modular Portability") states the interface the calls below
+ * follow: positions and box bounds in, per-particle group ids and kernel
+ * densities out.
+ *
+ * Conventions shared by every call
+ *   - Particles are indexed 0..n-1 in the caller's order.  All index arrays
+ *     (neighbour lists, hops, chain labels, boundary pairs) hold these
+ *     indices as uint32.  n must be < 2^31.
+ *   - Positions are AoS, 3 values per particle, in [0, box).  A coordinate
+ *     outside [0, box) (or NaN) makes the call fail with HOP_EINVAL.
+ *   - Pointers are device pointers unless a call says otherwise; calls
+ *     that also accept host memory say so and detect it themselves.
+ *   - The caller owns every input and output buffer.  The context owns its
+ *     scratch memory (grown on demand, kept between calls) and a stream.
+ *   - All calls are enqueued on the context's stream.  A call returns after
+ *     its work is enqueued, except where it must read a count back to the
+ *     host (noted per call); those calls synchronise the stream.
+ *   - Return codes are HOP_* below.  No C++ exception crosses the ABI.
+ *     hop_last_error() describes the last failure of a context.
+ */
+#ifndef HOP_H_
+#define HOP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HOP_OK = 0,
+    HOP_EINVAL = 1,      /* bad argument: sizes, ranges, null pointers, positions   */
+    HOP_ENOMEM = 2,      /* device allocation failed                                */
+    HOP_ECUDA = 3,       /* a CUDA runtime call failed (message in hop_last_error)  */
+    HOP_ETABLE = 4,      /* caller's edge capacity too small; *n_edges = required   */
+    HOP_ETIMEOUT = 5,    /* a device loop reached its iteration limit               */
+    HOP_EDEGENERATE = 6, /* more equidistant neighbours than the search buffer holds */
+    HOP_ENOMODEL = 7     /* learned radius requested but no network is loaded        */
+};
+
+/* How the kNN search picks each warp's first search radius.  All three give
+ * identical results: a search is certified only when at least Ndens
+ * particles fall inside a radius whose ball was scanned completely, and is
+ * otherwise repeated with a larger radius. */
+enum {
+    HOP_RADIUS_PLAIN = 0,   /* fixed base-grid cell: plain stencil expansion         */
+    HOP_RADIUS_COUNT = 1,   /* closed form from the 27 stencil cell counts          */
+    HOP_RADIUS_LEARNED = 2  /* the loaded MLP reads the 27 log-counts (hop_mlp_*)   */
+};
+
+typedef struct hop_params {
+    int32_t n_dens;       /* Ndens: list length incl. self (Sec. 2); 2..128        */
+    int32_t n_hop;        /* Nhop: hop candidates, 1..n_dens and <= 32              */
+    int32_t n_merge;      /* Nmerge: boundary search, 1..n_hop                      */
+    float delta_outer;    /* delta_outer: no halo below it (Sec. 2, step 1)         */
+    float delta_saddle;   /* delta_saddle: proto-halo merge threshold (step 4)      */
+    float delta_peak;     /* delta_peak: proto-halo threshold (step 2)              */
+    double box;           /* periodic box side L > 0                                */
+    int32_t pos_is_f64;   /* 0: positions are float32; 1: float64 (fp64 distances)  */
+    int32_t radius_mode;  /* HOP_RADIUS_*                                           */
+} hop_params;
+
+/* Fills p with the parameters the hot path is benchmarked with:
+ * Ndens 64, Nhop 16, Nmerge 4, delta 80 / 200 / 240, box 1, fp32, plain.
+ * (The paper's own defaults, Table 2, are Ndens = Nhop = 65, Nmerge = 4,
+ * delta_saddle = 2.5 delta_outer, delta_peak = 3 delta_outer.) */
+void hop_default_params(hop_params *p);
+
+typedef struct hop_ctx hop_ctx;
+
+/* Creates a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Returns HOP_OK and
+ * *out, or an error code and *out = NULL. */
+int hop_create(hop_ctx **out, int device, void *cuda_stream);
+/* Frees the context's scratch memory.  Safe on NULL. */
+void hop_destroy(hop_ctx *ctx);
+/* Changes the stream later calls enqueue on. */
+int hop_set_stream(hop_ctx *ctx, void *cuda_stream);
+/* Message of the last failure on this context ("" when none).  The string
+ * lives until the next call on the context. */
+const char *hop_last_error(const hop_ctx *ctx);
+/* Sets the queries per warp of the kNN search (4, 8, 16 or 32) and the
+ * number of search cells per radius (1 or 2); 0 keeps the current value.
+ * Results do not depend on these; only speed does. */
+int hop_set_tuning(hop_ctx *ctx, int32_t queries_per_warp, int32_t cells_per_radius);
+
+/*
+ * Step 1 (Sec. 2): Ndens nearest neighbours and kernel density.
+ *   pos   n x 3 float32 or float64 (params->pos_is_f64), AoS, device.
+ *   nbr   n x ld_nbr uint32: row i holds the first ld_nbr entries of i's
+ *         neighbour list in ascending (d^2, index) order, the particle itself
+ *         included (at d^2 = 0).  n_hop <= ld_nbr <= n_dens.  May be NULL.
+ *   dens  n float32: delta_i = (L^3/n) sum_{j in list} W(r_ij, h_i), W the M4
+ *         cubic spline with support 2h_i = r_k (the last list entry's
+ *         distance); +inf when all Ndens entries are at distance 0.
+ *   rk    n float32 or NULL: r_k, the distance to the Ndens-th entry.
+ * Distances are minimum-image, fp32 (fp64 when pos_is_f64) with one
+ * rounding per component difference.  Requires n >= n_dens.
+ */
+int hop_density(hop_ctx *ctx, const void *pos, int64_t n, const hop_params *params,
+                uint32_t *nbr, int32_t ld_nbr, float *dens, float *rk);
+
+/*
+ * Steps 2-3 (Sec. 2): hop to the densest of the first n_hop entries of each
+ * row of nbr (density desc, then smaller index; the particle itself may win),
+ * then follow hops to the root (a particle that is its own hop).
+ *   dens n float32, nbr n x ld_nbr uint32 (as written by hop_density),
+ *   hop n uint32 (may be NULL), chain n uint32 = index of the root.
+ * Fails with HOP_ETIMEOUT if following does not end (lists without self).
+ */
+int hop_link(hop_ctx *ctx, const float *dens, const uint32_t *nbr, int32_t ld_nbr,
+             int64_t n, int32_t n_hop, uint32_t *hop, uint32_t *chain);
+
+/*
+ * Merging step 3 (Sec. 2): boundary densities between chains.  For every i
+ * with dens_i >= delta_outer and every j among the first n_merge entries of
+ * row i, j != i, dens_j >= delta_outer, chain_i != chain_j, the pair
+ * {chain_i, chain_j} records s = (double)dens_i + (double)dens_j (twice the
+ * pair's average density, exact in fp64); each pair keeps its maximum.
+ *   edge_pair  cap uint64: (lo << 32) | hi with lo < hi the chain labels,
+ *   edge_sum   cap float64: the pair's maximum s,
+ * written in ascending edge_pair order.  *n_edges (host) = number of pairs.
+ * If cap < *n_edges, nothing is written and HOP_ETABLE is returned.
+ * Synchronises the stream (reads the pair count).
+ */
+int hop_boundaries(hop_ctx *ctx, const uint32_t *chain, const float *dens,
+                   const uint32_t *nbr, int32_t ld_nbr, int64_t n, int32_t n_merge,
+                   float delta_outer, uint64_t *edge_pair, double *edge_sum,
+                   int64_t cap, int64_t *n_edges);
+
+/*
+ * Merging steps 1, 2, 4, 5 (Sec. 2, Fig. 1): chains whose peak density is
+ * >= delta_peak are proto-halos; proto-halos whose boundary s >= 2
+ * delta_saddle merge, transitively; every other chain joins the proto-halo
+ * reached along its densest propagated boundary (the maximum spanning forest
+ * of the boundary graph with all proto-halos contracted, edges ordered by
+ * s desc, then lo, then hi); a chain that reaches none is in no group.
+ *   group n int32: -1 if dens_i < delta_outer or i's chain is in no group;
+ *   otherwise the group's rank when groups are ordered by their peak
+ *   (density desc, index asc).  *n_groups (host) = number of groups.
+ * Synchronises the stream.
+ */
+int hop_merge(hop_ctx *ctx, const uint32_t *chain, const float *dens, int64_t n,
+              const uint64_t *edge_pair, const double *edge_sum, int64_t n_edges,
+              float delta_outer, float delta_saddle, float delta_peak,
+              int32_t *group, int64_t *n_groups);
+
+/*
+ * The whole method in one call: steps 1-4 run in the context's spatially
+ * sorted order and only the results are written in the caller's order.
+ *   pos    n x 3 (float32 or float64), device OR host memory (pinned or
+ *          pageable; host buffers are copied in on the stream).
+ *   dens   n float32, device or host, or NULL.
+ *   group  n int32, device or host (as in hop_merge).
+ *   nbr    n x ld_nbr uint32 device, or NULL (as in hop_density).
+ *   chain  n uint32 device, or NULL (as in hop_link).
+ *   n_groups (host) number of groups.
+ * Synchronises the stream.  Output is identical for every radius_mode.
+ */
+int hop_run(hop_ctx *ctx, const void *pos, int64_t n, const hop_params *params,
+            float *dens, int32_t *group, int64_t *n_groups,
+            uint32_t *nbr, int32_t ld_nbr, uint32_t *chain);
+
+/* Counters and stage times (ms, CUDA events on the context stream) of the
+ * last hop_run / hop_density call. */
+typedef struct hop_stats {
+    double ms_sort, ms_radius, ms_knn, ms_link, ms_boundaries, ms_merge, ms_total;
+    int64_t candidates;      /* (query, candidate) distance evaluations          */
+    int64_t searches;        /* warp searches started (first tries + retries)    */
+    int64_t retries;         /* searches repeated with a larger radius           */
+    int64_t warps;           /* warp tasks (query chunks)                         */
+    int64_t n_chains, n_edges, n_groups;
+    int32_t knn_queries_per_warp, knn_cells_per_radius;
+} hop_stats;
+int hop_get_stats(const hop_ctx *ctx, hop_stats *out);
+
+/*
+ * Learned search radius (a 3-layer MLP, 27 -> 64 -> 64 -> 1, ReLU).
+ * Input: log(1 + count) of the 27 cells of the 3x3x3 stencil around a
+ * query chunk's cell, at the level whose cell size just covers the chunk.
+ * Output: log(R / cell size), R the largest Ndens-th-neighbour distance of
+ * the chunk.  Weights are BF16, accumulation FP32 (fp32 master copy for
+ * training).  The parameter vector layout is
+ *   W1[64][27], b1[64], W2[64][64], b2[64], W3[64], b3[1]   (HOP_MLP_NPARAM).
+ */
+#define HOP_MLP_IN 27
+#define HOP_MLP_HID 64
+#define HOP_MLP_NPARAM (64 * 27 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* Loads fp32 parameters (host) and the radius margin added to the predicted
+ * log radius before the search. */
+int hop_mlp_load(hop_ctx *ctx, const float *params_host, float log_margin);
+/* Copies the current fp32 master parameters to the host. */
+int hop_mlp_get(hop_ctx *ctx, float *params_host);
+
+/* After a hop_run or hop_density on pos, writes one training sample per
+ * query chunk: feat (n_chunks x 27 float32, device) and target (n_chunks
+ * float32, device) = log(max r_k over the chunk / cell size).  *n_chunks
+ * (host) is the number of samples; cap is the capacity of both buffers.
+ * Synchronises the stream. */
+int hop_mlp_samples(hop_ctx *ctx, float *feat, float *target, int64_t cap, int64_t *n_chunks);
+
+/* Forward pass over m samples (device): out[m] float32. */
+int hop_mlp_forward(hop_ctx *ctx, const float *feat, int64_t m, float *out);
+
+/* Mean-squared-error gradient over m samples (device): loss (host) and grad
+ * (HOP_MLP_NPARAM float32, device), both averaged over the samples, at the
+ * current BF16 weights. */
+int hop_mlp_grad(hop_ctx *ctx, const float *feat, const float *target, int64_t m,
+                 double *loss, float *grad);
+
+/* Trains in place with Adam (lr, beta1 0.9, beta2 0.999) on mini-batches of
+ * `batch` samples for `epochs` passes over the (device) data, from a
+ * deterministic sample order given by `seed`.  *final_loss (host) is the mean
+ * loss of the last epoch.  Synchronises the stream. */
+int hop_mlp_train(hop_ctx *ctx, const float *feat, const float *target, int64_t m,
+                  int32_t epochs, int32_t batch, float lr, uint64_t seed, double *final_loss);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOP_H_ */

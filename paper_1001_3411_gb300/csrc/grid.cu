@@ -1,0 +1,248 @@
+// Cell-grid build: Morton keys, radix sort, sorted float4 gather and the
+// dense cell table (the GPU counterpart of the kD-tree build and its
+// "resorted" position copy, Parallel HOP Sec. 4 "kD-tree Speedup"), plus
+// per-chunk stencil counts used to pick first search radii.
+#include "hop_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+__device__ __forceinline__ float4 make_rec(float x, float y, float z, uint32_t o)
+{
+    return make_float4(x, y, z, __uint_as_float(o));
+}
+__device__ __forceinline__ double4 make_rec(double x, double y, double z, uint32_t o)
+{
+    return make_double4(x, y, z, __longlong_as_double((long long)o));
+}
+
+template <typename T>
+__global__ void keys_kernel(const T *__restrict__ pos, int64_t n, T box, T inv_box,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ idx,
+                            uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        const bool ok = x >= T(0) && x < box && y >= T(0) && y < box && z >= T(0) && z < box;
+        if (!ok) {
+            atomicOr(err, kErrBadPos);
+            x = y = z = T(0);
+        }
+        const uint32_t qx = min((uint32_t)(x * inv_box * T(65536)), 65535u);
+        const uint32_t qy = min((uint32_t)(y * inv_box * T(65536)), 65535u);
+        const uint32_t qz = min((uint32_t)(z * inv_box * T(65536)), 65535u);
+        keys[i] = morton3(qx, qy, qz);
+        idx[i] = (uint32_t)i;
+    }
+}
+
+template <typename T>
+__global__ void gather_kernel(const T *__restrict__ pos, const uint32_t *__restrict__ perm,
+                              int64_t n, typename V4<T>::type *__restrict__ spos)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = perm[s];
+        spos[s] = make_rec(pos[3 * (int64_t)p], pos[3 * (int64_t)p + 1], pos[3 * (int64_t)p + 2], p);
+    }
+}
+
+// cellT[c] = first sorted index whose dense-level cell is >= c, for
+// c = 0 .. ncell (cellT[ncell] = n).
+__global__ void cell_table_kernel(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                                  int64_t ncell, uint32_t *__restrict__ cellT)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cs = s < n ? (int64_t)(keys[s] >> shift) : ncell;
+        const int64_t cp = s > 0 ? (int64_t)(keys[s - 1] >> shift) : -1;
+        for (int64_t c = cp + 1; c <= cs; ++c) cellT[c] = (uint32_t)s;
+    }
+}
+
+__device__ __forceinline__ void cell_range_g(const uint32_t *__restrict__ cellT,
+                                             const uint64_t *__restrict__ keys, int Ld, int l,
+                                             uint64_t code, uint32_t &a, uint32_t &b)
+{
+    if (l <= Ld) {
+        const int sh = 3 * (Ld - l);
+        a = cellT[code << sh];
+        b = cellT[(code + 1) << sh];
+        return;
+    }
+    const uint64_t pc = code >> (3 * (l - Ld));
+    uint32_t lo = cellT[pc], hi = cellT[pc + 1];
+    const int ksh = 3 * (kMaxLevel - l);
+    const uint64_t k0 = code << ksh, k1 = (code + 1) << ksh;
+    uint32_t L = lo, H = hi;
+    while (L < H) {
+        uint32_t m = (L + H) >> 1;
+        if (keys[m] < k0) L = m + 1; else H = m;
+    }
+    a = L;
+    H = hi;
+    while (L < H) {
+        uint32_t m = (L + H) >> 1;
+        if (keys[m] < k1) L = m + 1; else H = m;
+    }
+    b = L;
+}
+
+// One warp per chunk of Q sorted particles: the chunk's level (cell side
+// just >= its bounding-box extent) and the particle counts of the 3x3x3
+// cells around the cell holding the box centre.  Writes, as requested:
+//   feat[c][27] = log(1 + count), lvl[c], the closed-form radius
+//   R = side * (81 k / (4 pi sum counts))^(1/3) * exp(log_margin)
+//   (the radius of a ball holding k particles at the stencil's mean
+//   density), and the training target log(max r_k over the chunk / side).
+template <typename T>
+__global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
+                                  const uint64_t *__restrict__ keys,
+                                  const uint32_t *__restrict__ cellT, int Ld, int64_t n,
+                                  int64_t n_chunks, int Q, T box, T inv_box, int k,
+                                  float log_margin, float *__restrict__ chunk_r,
+                                  float *__restrict__ feat, uint8_t *__restrict__ lvl,
+                                  const float *__restrict__ rk_s, float *__restrict__ target)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ch = warp0; ch < n_chunks; ch += nwarps) {
+        const int64_t s0 = ch * Q;
+        const int nq = (int)min((int64_t)Q, n - s0);
+        const int64_t s = s0 + (lane < nq ? lane : 0);
+        const typename V4<T>::type v = spos[s];
+        T lx = v.x, ly = v.y, lz = v.z, hx = v.x, hy = v.y, hz = v.z;
+        float rk = (rk_s && lane < nq) ? rk_s[s] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = min(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = min(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = min(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = max(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = max(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = max(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+            rk = fmaxf(rk, __shfl_xor_sync(0xffffffffu, rk, o));
+        }
+        const T ext = max(hx - lx, max(hy - ly, hz - lz));
+        int l = kMaxLevel;
+        while (l > 2 && box / (T)(1 << l) < ext) --l;
+        const int G = 1 << l;
+        const T sc = inv_box * (T)G;
+        const int cx = min((int)floor((lx + hx) * T(0.5) * sc), G - 1);
+        const int cy = min((int)floor((ly + hy) * T(0.5) * sc), G - 1);
+        const int cz = min((int)floor((lz + hz) * T(0.5) * sc), G - 1);
+        uint32_t cnt = 0;
+        if (lane < 27) {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            const int rx = (cx + dx + G) % G, ry = (cy + dy + G) % G, rz = (cz + dz + G) % G;
+            uint32_t a, b;
+            cell_range_g(cellT, keys, Ld, l, morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz), a, b);
+            cnt = b - a;
+            if (feat) feat[ch * HOP_MLP_IN + lane] = log1pf((float)cnt);
+        }
+        uint32_t tot = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) {
+            const double side = (double)box / (double)G;
+            if (lvl) lvl[ch] = (uint8_t)l;
+            if (chunk_r) {
+                const double r = side * cbrt(81.0 * k / (4.0 * 3.14159265358979323846 * (double)max(tot, 1u)));
+                chunk_r[ch] = (float)(r * exp((double)log_margin));
+            }
+            if (target) target[ch] = logf(fmaxf(rk, 1e-30f) / (float)side);
+        }
+    }
+}
+
+template <typename T>
+int grid_build_t(hop_ctx *c, const T *pos, int64_t n, double box, void **spos_out,
+                 uint32_t **perm_out, uint64_t **keys_out, uint32_t **cellT_out, int *Ld_out)
+{
+    uint64_t *k0 = (uint64_t *)ctx_buf(c, S_KEY0, n * sizeof(uint64_t));
+    uint64_t *k1 = (uint64_t *)ctx_buf(c, S_KEY1, n * sizeof(uint64_t));
+    uint32_t *v0 = (uint32_t *)ctx_buf(c, S_VAL0, n * sizeof(uint32_t));
+    uint32_t *v1 = (uint32_t *)ctx_buf(c, S_VAL1, n * sizeof(uint32_t));
+    void *tmp = ctx_buf(c, S_SORT_TMP, radix_sort_scratch_bytes(n));
+    auto *spos = (typename V4<T>::type *)ctx_buf(c, S_SPOS, n * sizeof(typename V4<T>::type));
+    const int Ld = dense_level_for(n);
+    const int64_t ncell = int64_t(1) << (3 * Ld);
+    uint32_t *cellT = (uint32_t *)ctx_buf(c, S_CELLT, (ncell + 1) * sizeof(uint32_t));
+    if (!k0 || !k1 || !v0 || !v1 || !tmp || !spos || !cellT) return HOP_ENOMEM;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 32);
+    if (blocks < 1) blocks = 1;
+    keys_kernel<T><<<blocks, 256, 0, c->stream>>>(pos, n, (T)box, (T)(1.0 / box), k0, v0, c->d_err);
+    HOP_LAUNCH(c);
+    int rc = radix_sort_u64(c, k0, k1, v0, v1, n, 0, 48, tmp);
+    if (rc) return rc;
+    gather_kernel<T><<<blocks, 256, 0, c->stream>>>(pos, v0, n, spos);
+    HOP_LAUNCH(c);
+    int blocks2 = (int)std::min<int64_t>((n + 256) / 256, (int64_t)c->num_sms * 32);
+    cell_table_kernel<<<blocks2, 256, 0, c->stream>>>(k0, n, 3 * (kMaxLevel - Ld), ncell, cellT);
+    HOP_LAUNCH(c);
+    *spos_out = spos;
+    *perm_out = v0;
+    *keys_out = k0;
+    *cellT_out = cellT;
+    *Ld_out = Ld;
+    return HOP_OK;
+}
+
+template <typename T>
+int chunk_feat_launch(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                      int Ld, int64_t n, double box, int qpw, int k, float log_margin,
+                      float *chunk_r, float *feat, uint8_t *lvl, const float *rk_s, float *target)
+{
+    const int64_t n_chunks = (n + qpw - 1) / qpw;
+    int64_t blocks = (n_chunks + 7) / 8;
+    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 16);
+    if (blocks < 1) blocks = 1;
+    chunk_feat_kernel<T><<<(unsigned)blocks, 256, 0, c->stream>>>(
+        (const typename V4<T>::type *)spos, keys, cellT, Ld, n, n_chunks, qpw, (T)box,
+        (T)(1.0 / box), k, log_margin, chunk_r, feat, lvl, rk_s, target);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+}  // namespace
+
+int grid_build(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, void **spos_out,
+               uint32_t **perm_out, uint64_t **keys_out, uint32_t **cellT_out, int *Ld_out)
+{
+    if (p->pos_is_f64)
+        return grid_build_t<double>(c, (const double *)pos, n, p->box, spos_out, perm_out,
+                                    keys_out, cellT_out, Ld_out);
+    return grid_build_t<float>(c, (const float *)pos, n, p->box, spos_out, perm_out, keys_out,
+                               cellT_out, Ld_out);
+}
+
+// Closed-form first radius per chunk (HOP_RADIUS_COUNT), margin exp(0.25).
+int chunk_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                 int Ld, int64_t n, const hop_params *p, int qpw, float *chunk_r)
+{
+    const float margin = 0.25f;
+    if (p->pos_is_f64)
+        return chunk_feat_launch<double>(c, spos, keys, cellT, Ld, n, p->box, qpw, p->n_dens,
+                                         margin, chunk_r, nullptr, nullptr, nullptr, nullptr);
+    return chunk_feat_launch<float>(c, spos, keys, cellT, Ld, n, p->box, qpw, p->n_dens, margin,
+                                    chunk_r, nullptr, nullptr, nullptr, nullptr);
+}
+
+// Features, levels and (if rk_s) targets for every chunk.
+int chunk_features(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   int Ld, int64_t n, bool f64, double box, int qpw, float *feat, uint8_t *lvl,
+                   const float *rk_s, float *target)
+{
+    if (f64)
+        return chunk_feat_launch<double>(c, spos, keys, cellT, Ld, n, box, qpw, 64, 0.f, nullptr,
+                                         feat, lvl, rk_s, target);
+    return chunk_feat_launch<float>(c, spos, keys, cellT, Ld, n, box, qpw, 64, 0.f, nullptr, feat,
+                                    lvl, rk_s, target);
+}

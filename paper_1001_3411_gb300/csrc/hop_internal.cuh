@@ -1,0 +1,206 @@
+// Internal declarations of libhop: context, scratch arena, device helpers and
+// the launch functions each translation unit provides.  Nothing here is part
+// of the C ABI (include/hop.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hop.h"
+
+// ---------------------------------------------------------------- limits --
+// Morton keys hold 16 bits per axis (48-bit keys): levels 0..16 of the
+// octree over the box; level l has 2^l cells per axis.
+constexpr int kMaxLevel = 16;
+constexpr int kMaxDens = 128;    // Ndens limit (search buffer is 2 * Ndens + slack)
+constexpr int kHistBins = 32;    // 1/8-octave bins of d^2 used for selection
+
+// Device error word bits (atomicOr'ed by kernels, read by the host).
+enum : uint32_t {
+    kErrBadPos = 1u << 0,       // a coordinate outside [0, box) or NaN
+    kErrKnnRetry = 1u << 1,     // kNN search ran out of retries
+    kErrDegenerate = 1u << 2,   // more equidistant neighbours than the buffer holds
+    kErrChainLoop = 1u << 3,    // chain following hit its iteration limit
+    kErrTableFull = 1u << 4,    // boundary hash table overflow
+    kErrMergeLoop = 1u << 5,    // merge rounds hit their limit
+    kErrBadIndex = 1u << 6,     // an index array holds a value >= n
+};
+
+// Scratch slots owned by a context.  Each slot grows on demand.
+enum Slot {
+    S_POS_IN,      // device copy of host positions
+    S_KEY0, S_KEY1, S_VAL0, S_VAL1,   // radix sort ping-pong
+    S_SORT_TMP,    // per-block digit counts of the radix sort
+    S_SCAN,        // partial sums of the device-wide scan
+    S_SPOS,        // sorted positions (float4 / double4): x, y, z, original index
+    S_CELLT,       // cell start table at the dense level
+    S_CHUNK_R,     // per-chunk first search radius
+    S_CHUNK_LVL,   // per-chunk feature level (u8) / scratch
+    S_NBR_S,       // neighbour lists in sorted order (sorted indices)
+    S_DENS_S,      // densities in sorted order
+    S_RK_S,        // r_k in sorted order
+    S_DKEY,        // (density bits << 32) | ~original index
+    S_HOP, S_CHAIN,
+    S_HKEY, S_HVAL, // boundary hash table
+    S_EDGE_KEY, S_EDGE_SUM, S_EDGE_TMP,
+    S_MERGE,       // merge arrays (chains, components, ranks ...)
+    S_GROUP_S,
+    S_MISC,
+    S_MLP_TMP,
+    S_OUT_DENS, S_OUT_GROUP,            // device staging of host outputs
+    S_GROUP_OUT,                        // group ids in sorted order
+    S_ESORT_K0, S_ESORT_K1, S_ESORT_V0, S_ESORT_V1, S_ESORT_TMP,   // edge-list sort
+    S_COUNT
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct MlpState {
+    bool loaded = false;
+    float *w32 = nullptr;      // fp32 master parameters (device)
+    uint16_t *w16 = nullptr;   // bf16 copy used by every forward pass (device)
+    float *m = nullptr, *v = nullptr, *g = nullptr;   // Adam moments, gradient
+    float log_margin = 0.f;
+    int64_t step = 0;
+};
+
+struct hop_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    DevBuf buf[S_COUNT];
+    uint32_t *d_err = nullptr;          // device error word
+    unsigned long long *d_counters = nullptr;   // kNN counters (see kCnt*)
+    void *h_pinned = nullptr;           // small pinned host staging area
+    hop_stats stats{};
+    MlpState mlp;
+    int qpw = 8;                        // kNN queries per warp
+    int cpr = 1;                        // search cells per radius
+    // sorted state of the last density pass (for hop_mlp_samples)
+    int64_t last_n = 0;
+    int last_level_dense = 0;
+    int last_qpw = 8;
+    double last_box = 1.0;
+    bool last_f64 = false;
+    int last_ndens = 0;
+    const void *last_spos = nullptr;
+    const uint64_t *last_keys = nullptr;
+    const uint32_t *last_cellT = nullptr;
+    const float *last_rk = nullptr;
+    cudaEvent_t ev[12] = {};
+};
+
+// Counters slot indices in d_counters.
+enum { kCntCand = 0, kCntSearch, kCntRetry, kCntWarps, kCntQual, kCntEdges, kCntNum };
+
+// ------------------------------------------------------ host-side helpers --
+int ctx_fail(hop_ctx *c, int code, const std::string &msg);
+int ctx_cuda(hop_ctx *c, cudaError_t e, const char *what);
+void *ctx_buf(hop_ctx *c, Slot s, size_t bytes);   // nullptr on failure (err set)
+int ctx_check_device_error(hop_ctx *c);            // syncs; maps the error word
+
+#define HOP_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ctx_cuda((ctx), e_, #call); \
+    } while (0)
+
+#define HOP_LAUNCH(ctx)                                           \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return ctx_cuda((ctx), e_, "kernel launch"); \
+    } while (0)
+
+// ------------------------------------------------------ device helpers ---
+__host__ __device__ inline uint64_t spread3_16(uint32_t v)
+{
+    uint64_t x = v & 0xFFFFu;
+    x = (x | (x << 16)) & 0x0000FF0000FFull;
+    x = (x | (x << 8)) & 0x00F00F00F00Full;
+    x = (x | (x << 4)) & 0x0C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x249249249249ull;
+    return x;
+}
+
+__host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return spread3_16(x) | (spread3_16(y) << 1) | (spread3_16(z) << 2);
+}
+
+// Number of levels of the dense cell table for n particles: about 8
+// particles per dense cell on average, at least level 1.
+inline int dense_level_for(int64_t n)
+{
+    int l = 1;
+    while (l < 10 && (int64_t(1) << (3 * (l + 1))) * 8 <= n) ++l;
+    return l;
+}
+
+// ------------------------------------------------------------ launches ---
+// sort.cu
+int scan_exclusive_u32(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
+                       uint32_t *total_dev);
+size_t radix_sort_scratch_bytes(int64_t n);
+int radix_sort_u64(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
+                   uint32_t *&vals_alt, int64_t n, int begin_bit, int end_bit, void *scratch);
+int iota_u32(hop_ctx *c, uint32_t *out, int64_t n);
+
+// grid.cu
+int grid_build(hop_ctx *c, const void *pos, int64_t n, const hop_params *p,
+               void **spos_out, uint32_t **perm_out, uint64_t **keys_out, uint32_t **cellT_out,
+               int *level_dense_out);
+int chunk_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                 int level_dense, int64_t n, const hop_params *p, int qpw, float *chunk_r);
+int chunk_features(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   int level_dense, int64_t n, bool f64, double box, int qpw, float *feat,
+                   uint8_t *lvl, const float *rk_s, float *target);
+
+// knn.cu
+struct KnnArgs {
+    const void *spos;          // sorted positions (float4 / double4)
+    const uint64_t *keys;      // sorted Morton keys
+    const uint32_t *cellT;     // dense cell table
+    int level_dense;
+    int64_t n;
+    double box;
+    int k;                     // Ndens
+    int n_out;                 // list entries written per particle
+    int ld_out;                // row stride of nbr_s
+    const float *chunk_r;      // per-chunk first radius, or nullptr
+    float plain_r;             // first radius when chunk_r is null
+    uint32_t *nbr_s;           // n x ld_out sorted indices, or nullptr
+    float *dens_s;             // n
+    float *rk_s;               // n or nullptr
+};
+int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr);
+
+// link.cu
+int make_dkey(hop_ctx *c, const float *dens, const uint32_t *orig, int64_t n, uint64_t *dkey);
+int hop_links(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n, int n_hop,
+              uint32_t *hop, uint32_t *chain);
+int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr,
+                     int ld, int64_t n, int n_merge, float delta_outer,
+                     uint64_t **edge_key, double **edge_sum, int64_t *n_edges);
+int gather_f64(hop_ctx *c, const double *src, const uint32_t *idx, int64_t n, double *dst);
+int scatter_outputs(hop_ctx *c, const uint32_t *perm, int64_t n, const float *dens_s, float *dens,
+                    const int32_t *group_s, int32_t *group, const uint32_t *nbr_s, int ld_s,
+                    uint32_t *nbr, int ld, int n_cols, const uint32_t *chain_s, uint32_t *chain);
+
+// merge.cu
+int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_t n,
+                 const uint64_t *edge_key, const double *edge_sum, int64_t n_edges,
+                 float delta_outer, float delta_saddle, float delta_peak,
+                 int32_t *group, int64_t *n_groups);
+
+// mlp.cu
+int mlp_ensure(hop_ctx *c);
+int mlp_forward_dev(hop_ctx *c, const float *feat, int64_t m, float *out);
+void mlp_free(hop_ctx *c);
+int mlp_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+               int level_dense, int64_t n, const hop_params *p, int qpw, float *chunk_r);

@@ -1,0 +1,615 @@
+// Certified cell-stencil kNN fused with the M4 cubic-spline density
+// (HOP step 1, Parallel HOP Sec. 2).
+//
+// Layout.  Particles are sorted by a 48-bit Morton key, so every octree
+// cell at every level 0..16 is one contiguous range of the sorted float4
+// array {x, y, z, original index}.  A dense table gives the ranges of the
+// cells at one level (about 8 particles per cell); deeper cells are found by
+// binary search of the keys inside their dense ancestor.
+//
+// Work unit.  One warp takes Q = 32/P consecutive sorted particles (a chunk)
+// and serves them with P lanes each.  The warp scans every cell (at a level
+// matched to the search radius R) that meets the chunk's bounding box
+// dilated by R; candidates are staged in shared memory and each lane tests
+// every P-th staged candidate against its query.
+//
+// Selection.  A query keeps, in shared memory, every candidate seen so far
+// with d^2 <= tau (tau starts at R^2).  When the buffer passes 2 Ndens the
+// entries are histogrammed in 1/8-octave bins of d^2 below tau and tau drops
+// to the upper edge of the bin holding the Ndens-th entry, so tau stays an
+// upper bound of the Ndens-th distance of the candidates seen.  The search
+// is certified when every query holds >= Ndens entries: then all particles
+// within sqrt(tau) (<= R) were scanned and the Ndens nearest are exactly in
+// the buffer.  Otherwise the warp repeats with a larger R.
+//
+// Distances.  Inside a warp the box is unwrapped on each axis whose search
+// region crosses a face: coordinates >= L/2 move to x - L, exact by
+// Sterbenz' lemma, so d^2 = (xj - xi)^2 + ... has one rounding per
+// component difference whatever R was.  The density is a fixed-point sum of
+// kernel weights, so results do not depend on R, on the radius policy or on
+// the order candidates arrive in.
+#include "hop_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int kKnnWarps = 4;               // warps per block
+constexpr int kKnnThreads = kKnnWarps * 32;
+constexpr int kMaxTries = 96;
+constexpr uint32_t FULL = 0xffffffffu;
+
+template <typename T> struct Rec;
+template <> struct Rec<float> { float x, y, z; uint32_t s; };
+template <> struct Rec<double> { double x, y, z; uint32_t s; uint32_t pad; };
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+template <typename T> __device__ __forceinline__ uint32_t orig_of(const typename V4<T>::type &v);
+template <> __device__ __forceinline__ uint32_t orig_of<float>(const float4 &v) { return __float_as_uint(v.w); }
+template <> __device__ __forceinline__ uint32_t orig_of<double>(const double4 &v)
+{
+    return (uint32_t)__double_as_longlong(v.w);
+}
+
+// 1/8-octave bin of v relative to tau's own bin: bins 0..31, bin 31 holds
+// tau's octave-eighth, lower bins smaller values; bin 0 also holds everything
+// below.  Monotone in v for v >= 0.
+__device__ __forceinline__ int bin_base(float tau) { return (int)(__float_as_uint(tau) >> 20); }
+__device__ __forceinline__ int bin_base(double tau)
+{
+    return (int)((unsigned long long)__double_as_longlong(tau) >> 49);
+}
+__device__ __forceinline__ int bin_of(float v, int tb)
+{
+    int b = (int)(__float_as_uint(v) >> 20) - tb + (kHistBins - 1);
+    return min(max(b, 0), kHistBins - 1);
+}
+__device__ __forceinline__ int bin_of(double v, int tb)
+{
+    int b = (int)((unsigned long long)__double_as_longlong(v) >> 49) - tb + (kHistBins - 1);
+    return min(max(b, 0), kHistBins - 1);
+}
+// Largest value whose bin is <= b (b < 31), or -1 if that is below zero.
+__device__ __forceinline__ float bin_upper(float, int tb, int b)
+{
+    int e = tb - (kHistBins - 1) + b + 1;
+    if (e <= 0) return -1.f;
+    return __uint_as_float(((uint32_t)e << 20) - 1u);
+}
+__device__ __forceinline__ double bin_upper(double, int tb, int b)
+{
+    long long e = (long long)tb - (kHistBins - 1) + b + 1;
+    if (e <= 0) return -1.0;
+    return __longlong_as_double((long long)(((unsigned long long)e << 49) - 1ull));
+}
+
+// M4 cubic spline w(q) (Monaghan & Lattanzio 1985): W = w(r/h) / (pi h^3).
+template <typename T> __device__ __forceinline__ T m4(T q)
+{
+    if (q < T(1)) return T(1) - T(1.5) * q * q + T(0.75) * q * q * q;
+    if (q < T(2)) {
+        T t = T(2) - q;
+        return T(0.25) * t * t * t;
+    }
+    return T(0);
+}
+
+// Group (P lanes of one query) histogram of the buffer in 1/8-octave bins
+// below the buffer's largest entry; when the k-th entry falls below the
+// 31 bins the window moves down.  Returns bk (bin of the k-th entry), bo
+// (bin of the n_out-th entry), the count below bk and the window base tb.
+template <typename T, int P>
+__device__ void group_hist(const T *bd, int cnt, int *hist, int k, int n_out, int p,
+                           uint32_t gmask, int &tb, int &bk, int &bo, int &below_k, int &upto_k)
+{
+    T vmax = T(0);
+    for (int e = p; e < cnt; e += P) vmax = max(vmax, bd[e]);
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) vmax = max(vmax, __shfl_xor_sync(gmask, vmax, o));
+    tb = bin_base(vmax);
+    for (int guard = 0; guard < 96; ++guard) {
+        for (int b = p; b < kHistBins; b += P) hist[b] = 0;
+        __syncwarp(gmask);
+        for (int e = p; e < cnt; e += P) atomicAdd(&hist[bin_of(bd[e], tb)], 1);
+        __syncwarp(gmask);
+        int cum = 0;
+        bk = kHistBins - 1; bo = kHistBins - 1; below_k = 0; upto_k = cnt;
+        bool got_o = n_out <= 0;
+        for (int b = 0; b < kHistBins; ++b) {
+            const int h = hist[b];
+            if (!got_o && cum + h >= n_out) { bo = b; got_o = true; }
+            if (cum + h >= k) { bk = b; below_k = cum; upto_k = cum + h; break; }
+            cum += h;
+        }
+        __syncwarp(gmask);
+        // bin 0 also holds everything below the window: look lower
+        if ((bk > 0 && bo > 0) || tb <= kHistBins) break;
+        tb -= kHistBins - 1;
+    }
+}
+
+// Exact k-th smallest value of the buffer, given that it lies in bin bk and
+// below_k entries lie in lower bins; written to *out by the lane that finds it.
+template <typename T, int P>
+__device__ void group_kth(const T *bd, int cnt, int tb, int bk, int below_k, int k, int p,
+                          uint32_t gmask, T *out)
+{
+    for (int e = p; e < cnt; e += P) {
+        const T v = bd[e];
+        if (bin_of(v, tb) != bk) continue;
+        int lt = below_k, le = below_k;
+        for (int f = 0; f < cnt; ++f) {
+            const T u = bd[f];
+            if (bin_of(u, tb) != bk) continue;
+            lt += u < v;
+            le += u <= v;
+        }
+        if (lt < k && k <= le) *out = v;
+    }
+    __syncwarp(gmask);
+}
+
+template <typename T> struct KnnDev {
+    const typename V4<T>::type *spos;
+    const uint64_t *keys;
+    const uint32_t *cellT;
+    int level_dense;
+    int64_t n;
+    int64_t n_chunks;
+    T box, inv_box, half_box;
+    int k, n_out, ld_out, cap, buf;
+    const float *chunk_r;
+    float plain_r;
+    int cpr;
+    T norm;                       // box^3 / (n pi)
+    uint32_t *nbr_s;
+    float *dens_s;
+    float *rk_s;
+    unsigned long long *chunk_counter;
+    unsigned long long *counters;
+    uint32_t *err;
+};
+
+// Contiguous range of sorted particles in level-l cell `code`.
+__device__ __forceinline__ void cell_range(const uint32_t *__restrict__ cellT,
+                                           const uint64_t *__restrict__ keys, int Ld, int l,
+                                           uint64_t code, uint32_t &a, uint32_t &b)
+{
+    if (l <= Ld) {
+        const int sh = 3 * (Ld - l);
+        a = cellT[code << sh];
+        b = cellT[(code + 1) << sh];
+        return;
+    }
+    const int up = 3 * (l - Ld);
+    const uint64_t pc = code >> up;
+    uint32_t lo = cellT[pc], hi = cellT[pc + 1];
+    const int ksh = 3 * (kMaxLevel - l);
+    const uint64_t k0 = code << ksh, k1 = (code + 1) << ksh;
+    // lower_bound(k0)
+    uint32_t L = lo, H = hi;
+    while (L < H) {
+        uint32_t m = (L + H) >> 1;
+        if (keys[m] < k0) L = m + 1; else H = m;
+    }
+    a = L;
+    H = hi;
+    while (L < H) {
+        uint32_t m = (L + H) >> 1;
+        if (keys[m] < k1) L = m + 1; else H = m;
+    }
+    b = L;
+}
+
+template <typename T> __device__ __forceinline__ T wrapdiff(T xj, T xi, T box, T half)
+{
+    // Minimum-image difference with one rounding: the coordinate >= L/2 of
+    // the pair is moved by -L (exact) when the plain difference exceeds L/2.
+    T d = xj - xi;
+    if (d > half) return (xj - box) - xi;
+    if (d < -half) return xj - (xi - box);
+    return d;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
+{
+    constexpr int Q = 32 / P;
+    constexpr int TILE = sizeof(T) == 4 ? 128 : 64;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int q = lane / P, p = lane % P;
+    const uint32_t gmask = (P == 32) ? FULL : (((1u << P) - 1u) << (q * P));
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    // per-warp shared memory carve-up
+    const size_t bytes_tile = sizeof(Rec<T>) * TILE;
+    const size_t bytes_bd = sizeof(T) * (size_t)Q * a.buf;
+    const size_t bytes_bs = sizeof(uint32_t) * (size_t)Q * a.buf;
+    const size_t bytes_hist = sizeof(int) * Q * kHistBins;
+    const size_t bytes_misc = 68 * 4 + sizeof(T) * Q + 16;
+    const size_t per_warp = (bytes_tile + bytes_bd + bytes_bs + bytes_hist + bytes_misc + 15) & ~size_t(15);
+    unsigned char *wbase = smem_raw + per_warp * wib;
+    Rec<T> *tile = (Rec<T> *)wbase;
+    T *bd = (T *)(wbase + bytes_tile) + (size_t)q * a.buf;
+    uint32_t *bs = (uint32_t *)(wbase + bytes_tile + bytes_bd) + (size_t)q * a.buf;
+    int *hist = (int *)(wbase + bytes_tile + bytes_bd + bytes_bs) + q * kHistBins;
+    uint32_t *rs = (uint32_t *)(wbase + bytes_tile + bytes_bd + bytes_bs + bytes_hist);
+    uint32_t *ro = rs + 32;     // 33 entries
+    T *kthv = (T *)(ro + 33 + 3) ;
+
+    const T box = a.box, half = a.half_box, inv_box = a.inv_box;
+    const int k = a.k;
+    unsigned long long cand_acc = 0, search_acc = 0, retry_acc = 0, warp_acc = 0;
+
+    for (;;) {
+        unsigned long long ch = 0;
+        if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+        ch = __shfl_sync(FULL, ch, 0);
+        if ((int64_t)ch >= a.n_chunks) break;
+        ++warp_acc;
+        const int64_t s_first = (int64_t)ch * Q;
+        const int nq = (int)min((int64_t)Q, a.n - s_first);
+        const bool active = q < nq;
+        const int64_t sq = s_first + (active ? q : 0);
+        const typename V4<T>::type qv = a.spos[sq];
+        const T rqx = qv.x, rqy = qv.y, rqz = qv.z;
+
+        // bounding box of the chunk (inactive lanes repeat query 0)
+        T blx = rqx, bly = rqy, blz = rqz, bhx = rqx, bhy = rqy, bhz = rqz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            blx = min(blx, __shfl_xor_sync(FULL, blx, o));
+            bly = min(bly, __shfl_xor_sync(FULL, bly, o));
+            blz = min(blz, __shfl_xor_sync(FULL, blz, o));
+            bhx = max(bhx, __shfl_xor_sync(FULL, bhx, o));
+            bhy = max(bhy, __shfl_xor_sync(FULL, bhy, o));
+            bhz = max(bhz, __shfl_xor_sync(FULL, bhz, o));
+        }
+        const T ext_b = max(bhx - blx, max(bhy - bly, bhz - blz));
+
+        T R = a.chunk_r ? (T)a.chunk_r[ch] : (T)a.plain_r;
+        if (!(R > T(0))) R = box * T(1e-6);
+        T tau = R * R;
+        int cnt = 0;
+        bool certified = false;
+        int tries = 0;
+
+        while (!certified) {
+            ++search_acc;
+            // ---------------- search region for this radius
+            const T lox = blx - R, loy = bly - R, loz = blz - R;
+            const T hix = bhx + R, hiy = bhy + R, hiz = bhz + R;
+            const bool wx = lox < T(0) || hix >= box;
+            const bool wy = loy < T(0) || hiy >= box;
+            const bool wz = loz < T(0) || hiz >= box;
+            bool full = (ext_b + T(2) * R) >= half;
+            if (!full) {
+                if (wx && ((blx < half) != (bhx < half))) full = true;
+                if (wy && ((bly < half) != (bhy < half))) full = true;
+                if (wz && ((blz < half) != (bhz < half))) full = true;
+            }
+            // query and bbox in the warp's frame
+            const T qx = (wx && rqx >= half) ? rqx - box : rqx;
+            const T qy = (wy && rqy >= half) ? rqy - box : rqy;
+            const T qz = (wz && rqz >= half) ? rqz - box : rqz;
+            const T fblx = (wx && blx >= half) ? blx - box : blx;
+            const T fbhx = (wx && bhx >= half) ? bhx - box : bhx;
+            const T fbly = (wy && bly >= half) ? bly - box : bly;
+            const T fbhy = (wy && bhy >= half) ? bhy - box : bhy;
+            const T fblz = (wz && blz >= half) ? blz - box : blz;
+            const T fbhz = (wz && bhz >= half) ? bhz - box : bhz;
+
+            tau = full ? T(INFINITY) : R * R;
+            cnt = 0;
+
+            // level of the scanned cells: cell side >= R / cpr and >= (extent)/8
+            int l = 16, G = 1 << 16;
+            int c0x = 0, c0y = 0, c0z = 0, nx = 1, ny = 1, nz = 1;
+            if (!full) {
+                T want = max(R / (T)a.cpr, (ext_b + T(2) * R) * T(0.125));
+                T cells = box / want;   // >= 2^l
+                l = 1;
+                while (l < kMaxLevel && (T)(1 << (l + 1)) <= cells) ++l;
+                G = 1 << l;
+                const T sc = inv_box * (T)G;
+                c0x = (int)floor(lox * sc); c0y = (int)floor(loy * sc); c0z = (int)floor(loz * sc);
+                nx = (int)floor(hix * sc) - c0x + 1;
+                ny = (int)floor(hiy * sc) - c0y + 1;
+                nz = (int)floor(hiz * sc) - c0z + 1;
+                nx = min(nx, G); ny = min(ny, G); nz = min(nz, G);
+            }
+            const int ncells = full ? 1 : nx * ny * nz;
+            const T csz = box / (T)G;
+            const T R2c = R * R * T(1.00001) + box * box * T(1e-12);
+
+            for (int cb = 0; cb < ncells; cb += 32) {
+                // --------- one batch of up to 32 cells: ranges and prefix
+                uint32_t ra = 0, rb = 0;
+                const int ci = cb + lane;
+                if (full) {
+                    if (lane == 0) { ra = 0; rb = (uint32_t)a.n; }
+                } else if (ci < ncells) {
+                    const int ix = c0x + ci % nx, iy = c0y + (ci / nx) % ny, iz = c0z + ci / (nx * ny);
+                    const int rx = ((ix % G) + G) % G, ry = ((iy % G) + G) % G, rz = ((iz % G) + G) % G;
+                    T flx = (T)rx * csz, fly = (T)ry * csz, flz = (T)rz * csz;
+                    if (wx && rx >= (G >> 1)) flx -= box;
+                    if (wy && ry >= (G >> 1)) fly -= box;
+                    if (wz && rz >= (G >> 1)) flz -= box;
+                    T gx = max(T(0), max(flx - fbhx, fblx - (flx + csz)));
+                    T gy = max(T(0), max(fly - fbhy, fbly - (fly + csz)));
+                    T gz = max(T(0), max(flz - fbhz, fblz - (flz + csz)));
+                    if (gx * gx + gy * gy + gz * gz <= R2c) {
+                        const uint64_t code = morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz);
+                        cell_range(a.cellT, a.keys, a.level_dense, l, code, ra, rb);
+                    }
+                }
+                uint32_t len = rb - ra, inc = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(FULL, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const uint32_t total = __shfl_sync(FULL, inc, 31);
+                __syncwarp();
+                rs[lane] = ra;
+                ro[lane] = inc - len;
+                if (lane == 31) ro[32] = inc;
+                __syncwarp();
+
+                for (uint32_t t0 = 0; t0 < total; t0 += TILE) {
+                    const int m = (int)min((uint32_t)TILE, total - t0);
+                    // --------- stage candidates
+                    for (int e = lane; e < m; e += 32) {
+                        const uint32_t g = t0 + (uint32_t)e;
+                        int r = 0;
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1)
+                            if (ro[r + st] <= g) r += st;
+                        const uint32_t sidx = rs[r] + (g - ro[r]);
+                        const typename V4<T>::type v = a.spos[sidx];
+                        Rec<T> rec;
+                        if (full) {
+                            rec.x = v.x; rec.y = v.y; rec.z = v.z;
+                        } else {
+                            rec.x = (wx && v.x >= half) ? v.x - box : v.x;
+                            rec.y = (wy && v.y >= half) ? v.y - box : v.y;
+                            rec.z = (wz && v.z >= half) ? v.z - box : v.z;
+                        }
+                        rec.s = sidx;
+                        tile[e] = rec;
+                    }
+                    __syncwarp();
+                    cand_acc += (unsigned long long)m * (unsigned long long)nq;
+                    // --------- test staged candidates
+                    const int iters = (m + P - 1) / P;
+                    for (int it = 0; it < iters; ++it) {
+                        const int j = it * P + p;
+                        bool pass = false;
+                        T d2 = T(0);
+                        uint32_t sj = 0;
+                        if (j < m && active) {
+                            const Rec<T> c = tile[j];
+                            T dx, dy, dz;
+                            if (full) {
+                                dx = wrapdiff(c.x, rqx, box, half);
+                                dy = wrapdiff(c.y, rqy, box, half);
+                                dz = wrapdiff(c.z, rqz, box, half);
+                            } else {
+                                dx = c.x - qx; dy = c.y - qy; dz = c.z - qz;
+                            }
+                            d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                            sj = c.s;
+                            pass = d2 <= tau;
+                        }
+                        const uint32_t bal = __ballot_sync(FULL, pass);
+                        if (pass) {
+                            const int pos = cnt + __popc(bal & gmask & lt_mask);
+                            bd[pos] = d2;
+                            bs[pos] = sj;
+                        }
+                        cnt += __popc(bal & gmask);
+                        // --------- compaction when a buffer fills up
+                        if (((it & 3) == 3 || it == iters - 1) && __any_sync(FULL, cnt > a.cap)) {
+                            if (cnt > a.cap) {
+                                int tb, bk, bo, below_k, upto_k;
+                                group_hist<T, P>(bd, cnt, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
+                                // the bin edge shrinks the buffer only if the k-th entry's bin
+                                // is not crowded (candidates in a distant dense clump can share
+                                // one bin); otherwise cut at the exact k-th value
+                                T ntau = (bk < kHistBins - 1 && upto_k <= a.cap - 4 * P)
+                                             ? bin_upper(tau, tb, bk) : T(-1);
+                                if (!(ntau >= T(0))) {
+                                    group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
+                                    ntau = kthv[q];
+                                    __syncwarp(gmask);
+                                }
+                                // order-preserving in-place compaction, P entries per round
+                                int wp = 0;
+                                for (int base = 0; base < cnt; base += P) {
+                                    const int e = base + p;
+                                    T v = T(0);
+                                    uint32_t sv = 0;
+                                    bool keep = false;
+                                    if (e < cnt) { v = bd[e]; sv = bs[e]; keep = v <= ntau; }
+                                    const uint32_t kb = __ballot_sync(gmask, keep);
+                                    __syncwarp(gmask);
+                                    if (keep) {
+                                        const int dst = wp + __popc(kb & lt_mask);
+                                        bd[dst] = v;
+                                        bs[dst] = sv;
+                                    }
+                                    wp += __popc(kb);
+                                    __syncwarp(gmask);
+                                }
+                                cnt = wp;
+                                tau = ntau;
+                                if (cnt > a.cap) {
+                                    if (p == 0) atomicOr(a.err, kErrDegenerate);
+                                    cnt = a.cap;
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            // ---------------- certification
+            const bool ok = !active || cnt >= k;
+            if (__all_sync(FULL, ok)) {
+                certified = true;
+            } else {
+                ++retry_acc;
+                if (++tries >= kMaxTries || full) {
+                    if (lane == 0) atomicOr(a.err, kErrKnnRetry);
+                    break;
+                }
+                T f = T(1.25);
+                if (!ok) {
+                    T need = T(1.1) * cbrt((T)k / (T)max(cnt, 1));
+                    f = max(f, need);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) f = max(f, __shfl_xor_sync(FULL, f, o));
+                R *= min(f, T(8));
+            }
+        }
+        if (!certified) continue;
+
+        // -------------------- selection (per query group)
+        if (active) {
+            const int n_out = a.n_out;
+            int tb, bk, bo, below_k, upto_k;
+            group_hist<T, P>(bd, cnt, hist, k, n_out, p, gmask, tb, bk, bo, below_k, upto_k);
+            group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
+            const T vk = kthv[q];
+            // density: fixed-point sum of w(2 r / r_k) over entries with d^2 < r_k^2
+            unsigned long long wsum = 0;
+            const T rk = sqrt(vk);
+            if (vk > T(0)) {
+                const T inv_h = T(2) / rk;
+                for (int e = p; e < cnt; e += P) {
+                    const T v = bd[e];
+                    if (v < vk) {
+                        const T w = m4<T>(sqrt(v) * inv_h);
+                        wsum += (unsigned long long)(w * T(4294967296.0) + T(0.5));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < P; o <<= 1) wsum += __shfl_xor_sync(gmask, wsum, o);
+            // the n_out nearest in (d^2, original index) order
+            if (n_out > 0 && a.nbr_s) {
+                for (int e = p; e < cnt; e += P) {
+                    const T v = bd[e];
+                    if (bin_of(v, tb) > bo) continue;
+                    const uint32_t se = bs[e];
+                    uint32_t oe = 0xffffffffu;
+                    int rank = 0;
+                    for (int f = 0; f < cnt; ++f) {
+                        const T u = bd[f];
+                        if (u < v) { ++rank; continue; }
+                        if (u == v && f != e) {
+                            if (oe == 0xffffffffu) oe = orig_of<T>(a.spos[se]);
+                            const uint32_t of = orig_of<T>(a.spos[bs[f]]);
+                            rank += of < oe;
+                        }
+                    }
+                    if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                }
+            }
+            if (p == 0) {
+                float dens;
+                if (vk > T(0)) {
+                    const T h = rk * T(0.5);
+                    dens = (float)(a.norm * ((T)wsum * T(2.3283064365386963e-10)) / (h * h * h));
+                } else {
+                    dens = INFINITY;
+                }
+                a.dens_s[sq] = dens;
+                if (a.rk_s) a.rk_s[sq] = (float)rk;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[kCntCand], cand_acc);
+        atomicAdd(&a.counters[kCntSearch], search_acc);
+        atomicAdd(&a.counters[kCntRetry], retry_acc);
+        atomicAdd(&a.counters[kCntWarps], warp_acc);
+    }
+}
+
+template <typename T, int P> size_t knn_smem_per_warp(int buf)
+{
+    constexpr int Q = 32 / P;
+    constexpr int TILE = sizeof(T) == 4 ? 128 : 64;
+    size_t b = sizeof(Rec<T>) * TILE + sizeof(T) * (size_t)Q * buf + sizeof(uint32_t) * (size_t)Q * buf +
+               sizeof(int) * Q * kHistBins + 68 * 4 + sizeof(T) * Q + 16;
+    return (b + 15) & ~size_t(15);
+}
+
+template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
+{
+    constexpr int Q = 32 / P;
+    KnnDev<T> d;
+    d.spos = (const typename V4<T>::type *)a.spos;
+    d.keys = a.keys;
+    d.cellT = a.cellT;
+    d.level_dense = a.level_dense;
+    d.n = a.n;
+    d.n_chunks = (a.n + Q - 1) / Q;
+    d.box = (T)a.box;
+    d.inv_box = (T)(1.0 / a.box);
+    d.half_box = (T)(0.5 * a.box);
+    d.k = a.k;
+    d.n_out = a.n_out;
+    d.ld_out = a.ld_out;
+    d.cap = 2 * a.k;
+    d.buf = d.cap + 4 * P + 4;
+    d.chunk_r = a.chunk_r;
+    d.plain_r = a.plain_r;
+    d.cpr = cpr;
+    d.norm = (T)(a.box * a.box * a.box / ((double)a.n * 3.14159265358979323846));
+    d.nbr_s = a.nbr_s;
+    d.dens_s = a.dens_s;
+    d.rk_s = a.rk_s;
+    d.counters = c->d_counters;
+    d.chunk_counter = c->d_counters + kCntNum;
+    d.err = c->d_err;
+    HOP_CUDA(c, cudaMemsetAsync(d.chunk_counter, 0, sizeof(unsigned long long), c->stream));
+    const size_t smem = knn_smem_per_warp<T, P>(d.buf) * kKnnWarps;
+    auto kern = knn_kernel<T, P>;
+    HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKnnThreads, smem));
+    if (per_sm < 1) return ctx_fail(c, HOP_EINVAL, "kNN search buffer does not fit in shared memory");
+    int64_t blocks = (int64_t)per_sm * c->num_sms;
+    const int64_t need = (d.n_chunks + kKnnWarps - 1) / kKnnWarps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kKnnThreads, smem, c->stream>>>(d);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+}  // namespace
+
+int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr)
+{
+    if (a.k < 2 || a.k > kMaxDens) return ctx_fail(c, HOP_EINVAL, "n_dens out of range");
+    if (cpr != 1 && cpr != 2) cpr = 1;
+    switch (qpw) {
+    case 32: return f64 ? knn_run<double, 1>(c, a, cpr) : knn_run<float, 1>(c, a, cpr);
+    case 16: return f64 ? knn_run<double, 2>(c, a, cpr) : knn_run<float, 2>(c, a, cpr);
+    case 8: return f64 ? knn_run<double, 4>(c, a, cpr) : knn_run<float, 4>(c, a, cpr);
+    case 4: return f64 ? knn_run<double, 8>(c, a, cpr) : knn_run<float, 8>(c, a, cpr);
+    default: return ctx_fail(c, HOP_EINVAL, "queries per warp must be 4, 8, 16 or 32");
+    }
+}

@@ -1,0 +1,408 @@
+// HOP merging steps 1, 2, 4, 5 (Parallel HOP Sec. 2, Fig. 1) on the GPU.
+//
+//  M1  chains = roots (chain[i] == i) with density >= delta_outer, numbered
+//      densely by a scan; every boundary endpoint is such a root.
+//  M2  proto-halos: root density >= delta_peak.
+//  M3  edges sorted once in the strict merge order (s desc, lo asc, hi asc,
+//      lo/hi the roots' original indices) by two stable radix sorts, so an
+//      edge's position is its rank.
+//  M4  proto-halos joined by a direct boundary s >= 2 delta_saddle:
+//      connected components (hook to the smaller root + compress, until no
+//      edge joins two roots).  Each component is an owned set.
+//  M5  sub-peak chains: Boruvka rounds on the maximum spanning forest of the
+//      boundary graph with all owned sets contracted.  In a round every
+//      unowned component picks its best edge (smallest rank) to another
+//      component not both owned; it hooks to the other side (owned targets
+//      absorb it; a mutual pick keeps the smaller label as root).  Owned sets
+//      never pick, so no two owned sets meet.  Under a strict edge order the
+//      forest is unique, hence equal to the sequential Kruskal reading.
+//  M6  groups = owned sets, ranked by their peak key (density desc, index
+//      asc); group per particle with the delta_outer cut.
+#include "hop_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kMaxRounds = 64;
+
+__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ uint32_t key_orig(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
+
+__global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+                                 int64_t n, float d_o, uint32_t *__restrict__ flag,
+                                 uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = chain[i];
+        if (c >= (uint64_t)n || chain[c] != c) atomicOr(err, kErrBadIndex);
+        flag[i] = (c == (uint32_t)i && key_dens(dkey[i]) >= d_o) ? 1u : 0u;
+    }
+}
+
+__global__ void root_list_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+                                 int64_t n, float d_o, float d_p, const uint32_t *__restrict__ cid,
+                                 uint64_t *__restrict__ ckey, uint8_t *__restrict__ own)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (chain[i] != (uint32_t)i) continue;
+        const uint64_t k = dkey[i];
+        if (!(key_dens(k) >= d_o)) continue;
+        const uint32_t c = cid[i];
+        ckey[c] = k;
+        own[c] = key_dens(k) >= d_p ? 1 : 0;
+    }
+}
+
+// Edge endpoints -> dense chain ids; sort key for (lo_orig, hi_orig).
+__global__ void edge_prep_kernel(const uint64_t *__restrict__ ekey, const double *__restrict__ esum,
+                                 int64_t m, int64_t n, const uint32_t *__restrict__ chain,
+                                 const uint32_t *__restrict__ cid, const uint64_t *__restrict__ dkey,
+                                 float d_o, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
+                                 uint64_t *__restrict__ k1, uint32_t *__restrict__ v1,
+                                 uint32_t *__restrict__ err)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t lo = (uint32_t)(ekey[e] >> 32), hi = (uint32_t)ekey[e];
+        if (lo >= (uint64_t)n || hi >= (uint64_t)n || chain[lo] != lo || chain[hi] != hi ||
+            !(key_dens(dkey[lo]) >= d_o) || !(key_dens(dkey[hi]) >= d_o) || lo == hi) {
+            atomicOr(err, kErrBadIndex);
+            ea[e] = eb[e] = 0;
+            k1[e] = 0;
+            v1[e] = (uint32_t)e;
+            continue;
+        }
+        const uint32_t olo = key_orig(dkey[lo]), ohi = key_orig(dkey[hi]);
+        ea[e] = cid[lo];
+        eb[e] = cid[hi];
+        k1[e] = olo < ohi ? (((uint64_t)olo << 32) | ohi) : (((uint64_t)ohi << 32) | olo);
+        v1[e] = (uint32_t)e;
+        (void)esum;
+    }
+}
+
+__global__ void edge_key2_kernel(const double *__restrict__ esum, const uint32_t *__restrict__ order,
+                                 int64_t m, uint64_t *__restrict__ k2)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        k2[t] = ~(uint64_t)__double_as_longlong(esum[order[t]]);
+}
+
+__global__ void edge_permute_kernel(const uint32_t *__restrict__ order, int64_t m,
+                                    const uint32_t *__restrict__ ea, const uint32_t *__restrict__ eb,
+                                    const double *__restrict__ esum, uint32_t *__restrict__ sa,
+                                    uint32_t *__restrict__ sb, double *__restrict__ ss)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = order[t];
+        sa[t] = ea[e];
+        sb[t] = eb[e];
+        ss[t] = esum[e];
+    }
+}
+
+__global__ void iota_kernel(uint32_t *p, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)i;
+}
+
+__global__ void fill_kernel(uint32_t *p, int64_t n, uint32_t v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x)
+{
+    for (int g = 0; g < (1 << 24); ++g) {
+        const uint32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
+__global__ void proto_hook_kernel(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
+                                  const double *__restrict__ ss, int64_t m, double two_ds,
+                                  const uint8_t *__restrict__ own, uint32_t *parent,
+                                  uint32_t *changed)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = sa[t], b = sb[t];
+        if (!own[a] || !own[b] || !(ss[t] >= two_ds)) continue;
+        const uint32_t ra = find_root(parent, a), rb = find_root(parent, b);
+        if (ra == rb) continue;
+        atomicMin(&parent[max(ra, rb)], min(ra, rb));
+        *changed = 1u;
+    }
+}
+
+__global__ void compress_kernel(uint32_t *parent, int64_t C)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        parent[c] = find_root(parent, (uint32_t)c);
+}
+
+// Boruvka: every unowned component's smallest-rank eligible edge.
+__global__ void best_edge_kernel(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
+                                 int64_t m, const uint32_t *__restrict__ parent,
+                                 const uint8_t *__restrict__ own, uint32_t *__restrict__ best)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ca = parent[sa[t]], cb = parent[sb[t]];
+        if (ca == cb) continue;
+        const bool oa = own[ca], ob = own[cb];
+        if (oa && ob) continue;
+        if (!oa) atomicMin(&best[ca], (uint32_t)t);
+        if (!ob) atomicMin(&best[cb], (uint32_t)t);
+    }
+}
+
+__global__ void target_kernel(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
+                              int64_t C, const uint32_t *__restrict__ parent,
+                              const uint8_t *__restrict__ own, const uint32_t *__restrict__ best,
+                              uint32_t *__restrict__ tgt)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < C;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t y = kNone;
+        if (parent[x] == (uint32_t)x && !own[x] && best[x] != kNone) {
+            const uint32_t t = best[x];
+            const uint32_t ca = parent[sa[t]], cb = parent[sb[t]];
+            y = ca == (uint32_t)x ? cb : ca;
+        }
+        tgt[x] = y;
+    }
+}
+
+__global__ void hook_kernel(int64_t C, const uint8_t *__restrict__ own,
+                            const uint32_t *__restrict__ best, const uint32_t *__restrict__ tgt,
+                            uint32_t *parent, uint32_t *changed)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < C;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t y = tgt[x];
+        if (y == kNone) continue;
+        if (!own[y] && best[y] == best[x] && (uint32_t)x < y) continue;  // mutual: smaller stays root
+        parent[x] = y;
+        *changed = 1u;
+    }
+}
+
+__global__ void group_peak_kernel(int64_t C, const uint32_t *__restrict__ parent,
+                                  const uint8_t *__restrict__ own, const uint64_t *__restrict__ ckey,
+                                  unsigned long long *__restrict__ gpeak)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = parent[c];
+        if (own[r]) atomicMax(&gpeak[r], (unsigned long long)ckey[c]);
+    }
+}
+
+__global__ void group_flag_kernel(int64_t C, const uint32_t *__restrict__ parent,
+                                  const uint8_t *__restrict__ own, uint32_t *__restrict__ flag)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        flag[c] = (parent[c] == (uint32_t)c && own[c]) ? 1u : 0u;
+}
+
+__global__ void group_list_kernel(int64_t C, const uint32_t *__restrict__ flag,
+                                  const uint32_t *__restrict__ pos,
+                                  const unsigned long long *__restrict__ gpeak,
+                                  uint64_t *__restrict__ gk, uint32_t *__restrict__ gv)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[c]) continue;
+        gk[pos[c]] = ~(uint64_t)gpeak[c];
+        gv[pos[c]] = (uint32_t)c;
+    }
+}
+
+__global__ void group_rank_kernel(int64_t G, const uint32_t *__restrict__ gv, uint32_t *__restrict__ grank)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x)
+        grank[gv[g]] = (uint32_t)g;
+}
+
+__global__ void particle_group_kernel(const uint32_t *__restrict__ chain,
+                                      const uint64_t *__restrict__ dkey, int64_t n, float d_o,
+                                      const uint32_t *__restrict__ cid, int64_t C,
+                                      const uint32_t *__restrict__ parent,
+                                      const uint8_t *__restrict__ own,
+                                      const uint32_t *__restrict__ grank, int32_t *__restrict__ group,
+                                      uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = -1;
+        if (key_dens(dkey[i]) >= d_o) {
+            const uint32_t root = chain[i];
+            // a member above delta_outer has a root above it (hops go uphill)
+            if (!(key_dens(dkey[root]) >= d_o) || cid[root] >= (uint64_t)C) {
+                atomicOr(err, kErrBadIndex);
+            } else {
+                const uint32_t r = parent[cid[root]];
+                if (own[r]) g = (int32_t)grank[r];
+            }
+        }
+        group[i] = g;
+    }
+}
+
+inline int grid_for(hop_ctx *c, int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
+    return (int)std::max<int64_t>(b, 1);
+}
+
+inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_t n,
+                 const uint64_t *edge_key, const double *edge_sum, int64_t m, float d_o, float d_s,
+                 float d_p, int32_t *group, int64_t *n_groups)
+{
+    uint32_t *hp = (uint32_t *)c->h_pinned;
+    uint32_t *misc = (uint32_t *)ctx_buf(c, S_MISC, 256);
+    uint32_t *cid = (uint32_t *)ctx_buf(c, S_GROUP_S, (n + 1) * sizeof(uint32_t));
+    if (!misc || !cid) return HOP_ENOMEM;
+    uint32_t *d_total = misc, *d_changed = misc + 1, *d_merr = misc + 2;
+    HOP_CUDA(c, cudaMemsetAsync(misc, 0, 16, c->stream));
+    // M1
+    root_flag_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, d_merr);
+    HOP_LAUNCH(c);
+    int rc = scan_exclusive_u32(c, cid, cid, n, d_total);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 12, cudaMemcpyDeviceToHost, c->stream));
+    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hp[2] & kErrBadIndex) return ctx_fail(c, HOP_EINVAL, "chain labels are not roots of [0, n)");
+    const int64_t C = hp[0];
+    c->stats.n_chains = C;
+    c->stats.n_edges = m;
+    // arrays over chains and edges
+    const int64_t Cp = std::max<int64_t>(C, 1), mp = std::max<int64_t>(m, 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    const size_t o_ckey = take(Cp * 8), o_own = take(Cp), o_parent = take(Cp * 4),
+                 o_best = take(Cp * 4), o_tgt = take(Cp * 4), o_gpeak = take(Cp * 8),
+                 o_flag = take((Cp + 1) * 4), o_grank = take(Cp * 4), o_ea = take(mp * 4),
+                 o_eb = take(mp * 4), o_sa = take(mp * 4), o_sb = take(mp * 4), o_ss = take(mp * 8),
+                 o_k1 = take(mp * 8), o_k1b = take(mp * 8), o_v1 = take(mp * 4),
+                 o_v1b = take(mp * 4), o_gk = take(Cp * 8), o_gkb = take(Cp * 8),
+                 o_gv = take(Cp * 4), o_gvb = take(Cp * 4);
+    const size_t sort_tmp = std::max(radix_sort_scratch_bytes(mp), radix_sort_scratch_bytes(Cp));
+    const size_t o_tmp = take(sort_tmp);
+    char *base = (char *)ctx_buf(c, S_MERGE, off);
+    if (!base) return HOP_ENOMEM;
+    uint64_t *ckey = (uint64_t *)(base + o_ckey);
+    uint8_t *own = (uint8_t *)(base + o_own);
+    uint32_t *parent = (uint32_t *)(base + o_parent), *best = (uint32_t *)(base + o_best),
+             *tgt = (uint32_t *)(base + o_tgt), *flag = (uint32_t *)(base + o_flag),
+             *grank = (uint32_t *)(base + o_grank);
+    unsigned long long *gpeak = (unsigned long long *)(base + o_gpeak);
+    uint32_t *ea = (uint32_t *)(base + o_ea), *eb = (uint32_t *)(base + o_eb),
+             *sa = (uint32_t *)(base + o_sa), *sb = (uint32_t *)(base + o_sb);
+    double *ss = (double *)(base + o_ss);
+    uint64_t *k1 = (uint64_t *)(base + o_k1), *k1b = (uint64_t *)(base + o_k1b);
+    uint32_t *v1 = (uint32_t *)(base + o_v1), *v1b = (uint32_t *)(base + o_v1b);
+    uint64_t *gk = (uint64_t *)(base + o_gk), *gkb = (uint64_t *)(base + o_gkb);
+    uint32_t *gv = (uint32_t *)(base + o_gv), *gvb = (uint32_t *)(base + o_gvb);
+    void *tmp = base + o_tmp;
+
+    HOP_CUDA(c, cudaMemsetAsync(own, 0, Cp, c->stream));
+    root_list_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, d_p, cid, ckey, own);
+    HOP_LAUNCH(c);
+    // M3: strict order
+    if (m > 0) {
+        edge_prep_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(edge_key, edge_sum, m, n, chain, cid,
+                                                               dkey, d_o, ea, eb, k1, v1, d_merr);
+        HOP_LAUNCH(c);
+        rc = radix_sort_u64(c, k1, k1b, v1, v1b, m, 0, 64, tmp);
+        if (rc) return rc;
+        edge_key2_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(edge_sum, v1, m, k1);
+        HOP_LAUNCH(c);
+        rc = radix_sort_u64(c, k1, k1b, v1, v1b, m, 0, 64, tmp);
+        if (rc) return rc;
+        edge_permute_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(v1, m, ea, eb, edge_sum, sa, sb, ss);
+        HOP_LAUNCH(c);
+    }
+    // M4: proto-halo components
+    iota_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+    HOP_LAUNCH(c);
+    int rounds = 0;
+    for (; m > 0 && rounds < kMaxRounds; ++rounds) {
+        HOP_CUDA(c, cudaMemsetAsync(d_changed, 0, 4, c->stream));
+        proto_hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(sa, sb, ss, m, 2.0 * (double)d_s, own,
+                                                                parent, d_changed);
+        HOP_LAUNCH(c);
+        compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+        HOP_LAUNCH(c);
+        HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 12, cudaMemcpyDeviceToHost, c->stream));
+        HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (hp[2] & kErrBadIndex) return ctx_fail(c, HOP_EINVAL, "boundary pair is not a pair of chains above delta_outer");
+        if (!hp[1]) break;
+    }
+    if (rounds >= kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "proto-halo merge did not converge");
+    // M5: Boruvka over sub-peak chains
+    for (rounds = 0; m > 0 && rounds < kMaxRounds; ++rounds) {
+        HOP_CUDA(c, cudaMemsetAsync(d_changed, 0, 4, c->stream));
+        fill_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(best, C, kNone);
+        HOP_LAUNCH(c);
+        best_edge_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(sa, sb, m, parent, own, best);
+        HOP_LAUNCH(c);
+        target_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(sa, sb, C, parent, own, best, tgt);
+        HOP_LAUNCH(c);
+        hook_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, own, best, tgt, parent, d_changed);
+        HOP_LAUNCH(c);
+        compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+        HOP_LAUNCH(c);
+        HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 8, cudaMemcpyDeviceToHost, c->stream));
+        HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (!hp[1]) break;
+    }
+    if (rounds >= kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "sub-peak merge did not converge");
+    // owned status of a root is its own (owned sets never hook); M6: groups
+    HOP_CUDA(c, cudaMemsetAsync(gpeak, 0, Cp * 8, c->stream));
+    group_peak_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, own, ckey, gpeak);
+    HOP_LAUNCH(c);
+    group_flag_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, own, flag);
+    HOP_LAUNCH(c);
+    uint32_t *gpos = tgt;   // reuse
+    rc = scan_exclusive_u32(c, flag, gpos, C, d_total);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 4, cudaMemcpyDeviceToHost, c->stream));
+    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int64_t G = C > 0 ? hp[0] : 0;
+    if (G > 0) {
+        group_list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, gpeak, gk, gv);
+        HOP_LAUNCH(c);
+        rc = radix_sort_u64(c, gk, gkb, gv, gvb, G, 0, 64, tmp);
+        if (rc) return rc;
+        group_rank_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, gv, grank);
+        HOP_LAUNCH(c);
+    }
+    particle_group_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, C, parent,
+                                                                own, grank, group, c->d_err);
+    HOP_LAUNCH(c);
+    *n_groups = G;
+    c->stats.n_groups = G;
+    return HOP_OK;
+}
