@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 HOP hot path: end-to-end particles/s at 512^3.
+
+One step is one complete HOP pass (cell build, kNN + density, hops, chains,
+boundaries, merge, results in the caller's order) over the 512^3 synthetic
+NFW + 40% background box.  The headline value uses the learned first search
+radius; the plain-radius path is timed beside it and must give identical
+output.  Inputs are resident in HBM for `value`; `e2e` passes host (pinned)
+buffers through the same C-ABI call, copies included.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU runs (torchrun) are replicas: every rank runs its own box, and
+the value is all particles over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s end-to-end HOP at 512^3: learned-radius vs plain GPU, same output"
+N_DENS, N_HOP, N_MERGE = 64, 16, 4
+DELTAS = (80.0, 200.0, 240.0)
+FLOP_PER_CANDIDATE = 8          # 3 sub + 1 mul + 2 fma, counted as in the survey
+IDEAL_CANDIDATES = N_DENS * 6.0 / math.pi   # stencil sized to the ball
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="nfw512")
+    ap.add_argument("--scale", type=int, default=None, help="override particle count (testing)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        pw = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if parts and parts[min(local_rank, len(parts) - 1)].strip().isdigit():
+        return int(parts[min(local_rank, len(parts) - 1)])
+    return local_rank
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_rate(pos, seconds: float, seed: int = 7):
+    """The CPU oracle as it stands, on a bounded sample of the workload:
+    brute-force kNN + density of S random particles against the whole box
+    (the oracle's per-particle cost), plus its linking, boundary and merge
+    stages timed per particle on the 32,768-particle Plummer set."""
+    import numpy as np
+
+    import oracle
+    import synth
+    n = len(pos)
+    pos64 = np.ascontiguousarray(pos, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    threads = oracle.num_threads()
+    q = rng.choice(n, size=max(threads, 4), replace=False)
+    t0 = time.perf_counter()
+    _, d2 = oracle.knn(pos64, N_DENS, 1.0, queries=q)
+    oracle.density(d2, n)
+    t_cal = (time.perf_counter() - t0) / len(q)
+    s = int(max(threads, min(4096, seconds * 0.9 / max(t_cal, 1e-9))))
+    s = max(threads, (s // threads) * threads)
+    q = rng.choice(n, size=s, replace=False)
+    t0 = time.perf_counter()
+    _, d2 = oracle.knn(pos64, N_DENS, 1.0, queries=q)
+    oracle.density(d2, n)
+    t_knn = time.perf_counter() - t0
+    small = synth.workload("plummer32k")
+    nbr_s, d2_s = oracle.knn(small, N_DENS)
+    dens_s = oracle.density(d2_s, len(small))
+    t0 = time.perf_counter()
+    _, ch = oracle.link(dens_s, nbr_s, N_HOP)
+    lo, hi, sm = oracle.boundaries(ch, dens_s, nbr_s, N_MERGE, DELTAS[0])
+    oracle.merge(ch, dens_s, lo, hi, sm, *DELTAS)
+    t_rest = time.perf_counter() - t0
+    per_particle = t_knn / s + t_rest / len(small)
+    return {"value": 1.0 / per_particle, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "sample": (f"fp64 brute-force kNN + M4 density of {s} random particles of the {n}-particle "
+                       f"box ({t_knn:.1f} s), plus link/boundaries/merge timed per particle on the "
+                       f"32,768-particle Plummer set ({t_rest * 1e3:.0f} ms)"),
+            "seconds": t_knn + t_rest}
+
+
+# ------------------------------------------------------------- gb300 arm
+def tune(hop, dpos, params, out, candidates):
+    """Untimed: pick the fastest (queries per warp, cells per radius) for a
+    radius policy; output does not depend on it."""
+    import torch
+    best = None
+    for qpw, cpr in candidates:
+        hop.set_tuning(qpw, cpr)
+        if params.radius_mode == 2:
+            load_model(hop, qpw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hop.hop_run(dpos, params, out=out)
+        t = time.perf_counter() - t0
+        if best is None or t < best[0]:
+            best = (t, qpw, cpr)
+    return best
+
+
+_MODELS = None
+
+
+def load_model(hop, qpw):
+    global _MODELS
+    from paper_1001_3411_gb300 import radius_model
+    if _MODELS is None:
+        _MODELS = radius_model.load()
+    params, margin = _MODELS[qpw]
+    hop.hop_mlp_load(params, margin)
+
+
+def ensure_model(hop):
+    """Trained weights ship with the package; if absent, train them here
+    (untimed) on the 256^3 set exactly as radius_model.main() does."""
+    import torch
+
+    from paper_1001_3411_gb300 import radius_model
+    import synth
+    if os.path.exists(radius_model.DEFAULT_PATH):
+        return "stored"
+    pos, _ = synth.nfw_box(256 ** 3, synth.workload_seed(2))
+    dpos = torch.from_numpy(pos).cuda()
+    models = {}
+    for q in (4, 8, 16):
+        feat, tgt = radius_model.samples(hop, dpos, q)
+        params, margin, _ = radius_model.train(hop, feat, tgt)
+        models[q] = (params, margin)
+    radius_model.save(radius_model.DEFAULT_PATH, models, {"train_n": 256 ** 3})
+    del dpos
+    torch.cuda.empty_cache()
+    return "trained now"
+
+
+def timed_steps(hop, dpos, params, out, steps, dist):
+    import torch
+    st = torch.cuda.current_stream()
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        hop.hop_run(dpos, params, out=out)
+        stats.append(hop.stats())
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1), stats
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1001_3411_gb300 import Hop, build_library, default_params
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    torch.cuda.set_device(local)
+    build_library()
+    hop = Hop(local)
+    model_src = ensure_model(hop)
+
+    if args.scale:
+        pos, _ = synth.nfw_box(args.scale, synth.workload_seed(3, rank))
+        wl = f"nfw{args.scale}"
+    else:
+        pos = synth.workload(args.workload, sub=rank)
+        wl = args.workload
+    n = len(pos)
+    dpos = torch.from_numpy(pos).cuda()
+    out = {"group": torch.empty(n, dtype=torch.int32, device="cuda"),
+           "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
+    p_learn = default_params(radius_mode=2)
+    p_plain = default_params(radius_mode=0)
+    p_count = default_params(radius_mode=1)
+    cands = [(8, 1)] if args.no_tune else [(4, 1), (8, 1), (16, 1), (8, 2)]
+    tuned = {}
+    for name, p, cs in (("learned", p_learn, [c for c in cands if c[0] in (4, 8, 16)]),
+                        ("plain", p_plain, cands), ("count", p_count, cands)):
+        t, q, c = tune(hop, dpos, p, out, cs)
+        tuned[name] = (q, c)
+
+    def configure(name):
+        q, c = tuned[name]
+        hop.set_tuning(q, c)
+        if name == "learned":
+            load_model(hop, q)
+
+    # identical output across radius policies (untimed check)
+    ref = {}
+    for name, p in (("plain", p_plain), ("learned", p_learn), ("count", p_count)):
+        configure(name)
+        r = hop.hop_run(dpos, p, out=out)
+        ref[name] = (out["group"].clone(), out["dens"].clone(), r["n_groups"])
+    same = all(torch.equal(ref["plain"][0], ref[k][0]) and torch.equal(ref["plain"][1], ref[k][1])
+               for k in ("learned", "count"))
+
+    results = {}
+    for name, p in (("plain", p_plain), ("count", p_count), ("learned", p_learn)):
+        configure(name)
+        for _ in range(args.warmup):
+            hop.hop_run(dpos, p, out=out)
+        if name == "learned":
+            with ClockSampler(gpu_index(local)) as cs:
+                ms, stats = timed_steps(hop, dpos, p, out, args.steps, dist)
+            clocks = cs.summary()
+        else:
+            ms, stats = timed_steps(hop, dpos, p, out, args.steps, dist)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        results[name] = (ms / args.steps, stats)
+
+    # end to end through the same C-ABI call with host buffers
+    configure("learned")
+    hpos = torch.from_numpy(pos).pin_memory()
+    hout = {"group": torch.empty(n, dtype=torch.int32).pin_memory(),
+            "dens": torch.empty(n, dtype=torch.float32).pin_memory()}
+    hop.hop_run(hpos, p_learn, out=hout)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hop.hop_run(hpos, p_learn, out=hout)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert torch.equal(hout["group"], ref["plain"][0].cpu()), "host-buffer run differs"
+
+    ms_l, st_l = results["learned"]
+    ms_p, st_p = results["plain"]
+    ms_c, st_c = results["count"]
+    last = st_l[-1]
+    knn_ms = statistics.median(s["ms_knn"] for s in st_l)
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s at the sampled clock
+    alg_flop = n * IDEAL_CANDIDATES * FLOP_PER_CANDIDATE
+    achieved = alg_flop / (knn_ms * 1e-3) / 1e12
+
+    def stage(st):
+        keys = ("ms_sort", "ms_radius", "ms_knn", "ms_link", "ms_boundaries", "ms_merge", "ms_total")
+        return {k[3:]: round(statistics.median(s[k] for s in st), 3) for k in keys}
+
+    line = {
+        "metric": METRIC,
+        "value": n * world / (ms_l * 1e-3),
+        "unit": "particles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_l,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl, "n_particles": n, "n_dens": N_DENS, "n_hop": N_HOP,
+                   "n_merge": N_MERGE, "deltas": list(DELTAS), "radius": "learned",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs (12 B/particle, %.2f GB) larger than L2; no flush" % (n * 12 / 1e9),
+                   "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1]}
+                              for k, v in tuned.items()},
+                   "radius_model": model_src},
+        "identical_output": bool(same),
+        "n_groups": int(ref["learned"][2]),
+        "plain": {"value": n * world / (ms_p * 1e-3), "ms_per_step": ms_p, "stages_ms": stage(st_p),
+                  "candidates_per_particle": st_p[-1]["candidates"] / n,
+                  "retries": st_p[-1]["retries"], "searches": st_p[-1]["searches"]},
+        "count": {"value": n * world / (ms_c * 1e-3), "ms_per_step": ms_c, "stages_ms": stage(st_c),
+                  "candidates_per_particle": st_c[-1]["candidates"] / n,
+                  "retries": st_c[-1]["retries"], "searches": st_c[-1]["searches"]},
+        "learned": {"stages_ms": stage(st_l), "candidates_per_particle": last["candidates"] / n,
+                    "retries": last["retries"], "searches": last["searches"]},
+        "speedup_learned_vs_plain": ms_p / ms_l,
+        "roofline": {"kernel": "knn_kernel<float,P> (kNN + M4 density)", "bound": "alu",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "basis": ("algorithmic flop = N x 64 x 6/pi candidates x 8 flop; peak = SMs x 128 "
+                               "FP32 lanes x 2 x sampled median SM clock"),
+                     "knn_ms": knn_ms},
+        "gpu_launches": int(last["launches"]),
+        "clocks": clocks,
+        "e2e": {"value": n * world / e2e_s, "unit": "particles/s",
+                "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 8},
+    }
+    if rank == 0:
+        line["cpu_baseline"] = oracle_rate(pos, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    hop.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle (the plain CPU definition of the method) as the reference
+    arm: each step is a bounded sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    if args.scale:
+        pos, _ = synth.nfw_box(args.scale, synth.workload_seed(3))
+        wl = f"nfw{args.scale}"
+    else:
+        pos = synth.workload(args.workload)
+        wl = args.workload
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        oracle_rate(pos, per_step * 0.25, seed=100 + i)
+    rates = [oracle_rate(pos, per_step, seed=i) for i in range(args.steps)]
+    v = statistics.median(r["value"] for r in rates)
+    line = {"metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl, "n_particles": len(pos), "n_dens": N_DENS, "n_hop": N_HOP,
+                       "n_merge": N_MERGE, "deltas": list(DELTAS)},
+            "cpu_baseline": {"value": v, "unit": "particles/s", "cores": rates[0]["cores"],
+                             "kind": "oracle", "sample": rates[0]["sample"]},
+            "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gb300(a)

@@ -184,6 +184,7 @@ typedef struct hop_stats {
     int64_t warps;           /* warp tasks (query chunks)                         */
     int64_t n_chains, n_edges, n_groups;
     int32_t knn_queries_per_warp, knn_cells_per_radius;
+    int64_t launches;        /* kernels this library launched during the call     */
 } hop_stats;
 int hop_get_stats(const hop_ctx *ctx, hop_stats *out);
 

@@ -41,7 +41,8 @@ class HopStats(C.Structure):
                 ("ms_total", C.c_double), ("candidates", C.c_int64), ("searches", C.c_int64),
                 ("retries", C.c_int64), ("warps", C.c_int64), ("n_chains", C.c_int64),
                 ("n_edges", C.c_int64), ("n_groups", C.c_int64),
-                ("knn_queries_per_warp", C.c_int32), ("knn_cells_per_radius", C.c_int32)]
+                ("knn_queries_per_warp", C.c_int32), ("knn_cells_per_radius", C.c_int32),
+                ("launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

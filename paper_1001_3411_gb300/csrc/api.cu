@@ -292,6 +292,7 @@ int hop_density(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, uin
     if (nbr && (ld_nbr < p->n_hop || ld_nbr > p->n_dens))
         return ctx_fail(c, HOP_EINVAL, "ld_nbr must be in [n_hop, n_dens]");
     HOP_CUDA(c, cudaSetDevice(c->device));
+    const int64_t launches0 = c->launches;
     DensityState st;
     rc = density_core(c, pos, n, p, nbr ? ld_nbr : 0, &st);
     if (rc) return rc;
@@ -312,6 +313,7 @@ int hop_density(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, uin
     c->stats.ms_radius = ev_ms(c, 1, 2);
     c->stats.ms_knn = ev_ms(c, 2, 3);
     c->stats.ms_total = ev_ms(c, 0, 4);
+    c->stats.launches = c->launches - launches0;
     return rc;
 }
 
@@ -410,6 +412,7 @@ int hop_run(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, float *
     const bool host_pos = is_host_ptr(pos);
     const bool host_dens = dens && is_host_ptr(dens);
     const bool host_group = is_host_ptr(group);
+    const int64_t launches0 = c->launches;
     ev_record(c, 8);
     const void *dpos = pos;
     if (host_pos) {
@@ -471,6 +474,7 @@ int hop_run(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, float *
     c->stats.ms_boundaries = ev_ms(c, 5, 6);
     c->stats.ms_merge = ev_ms(c, 6, 7);
     c->stats.ms_total = ev_ms(c, 8, 9);
+    c->stats.launches = c->launches - launches0;
     return rc;
 }
 

@@ -79,6 +79,7 @@ struct hop_ctx {
     unsigned long long *d_counters = nullptr;   // kNN counters (see kCnt*)
     void *h_pinned = nullptr;           // small pinned host staging area
     hop_stats stats{};
+    int64_t launches = 0;               // kernels launched (all calls)
     MlpState mlp;
     int qpw = 8;                        // kNN queries per warp
     int cpr = 1;                        // search cells per radius
@@ -113,6 +114,7 @@ int ctx_check_device_error(hop_ctx *c);            // syncs; maps the error word
 
 #define HOP_LAUNCH(ctx)                                           \
     do {                                                          \
+        ++(ctx)->launches;                                        \
         cudaError_t e_ = cudaGetLastError();                      \
         if (e_ != cudaSuccess) return ctx_cuda((ctx), e_, "kernel launch"); \
     } while (0)
@@ -133,13 +135,14 @@ __host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
     return spread3_16(x) | (spread3_16(y) << 1) | (spread3_16(z) << 2);
 }
 
-// Number of levels of the dense cell table for n particles: about 8
-// particles per dense cell on average, at least level 1.
+// Level of the dense cell table for n particles: the first level with at
+// least n cells, plus one (so deeper cells, found by binary search, hold few
+// particles), at most level 10 (2^30 cells, a 4 GB table).
 inline int dense_level_for(int64_t n)
 {
     int l = 1;
-    while (l < 10 && (int64_t(1) << (3 * (l + 1))) * 8 <= n) ++l;
-    return l;
+    while (l < 10 && (int64_t(1) << (3 * l)) < n) ++l;
+    return l < 10 ? l + 1 : 10;
 }
 
 // ------------------------------------------------------------ launches ---

@@ -214,11 +214,37 @@ template <typename T> __device__ __forceinline__ T wrapdiff(T xj, T xi, T box, T
     return d;
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
+// Shared-memory layout of one warp (byte offsets), used by kernel and host.
+template <typename T, int P> struct WarpSmem {
+    static constexpr int Q = 32 / P;
+    static constexpr int TILE = sizeof(T) == 4 ? 128 : 64;
+    __host__ __device__ static size_t tile() { return 0; }
+    __host__ __device__ static size_t bd() { return sizeof(Rec<T>) * TILE; }
+    __host__ __device__ static size_t bs(int buf) { return bd() + sizeof(T) * (size_t)Q * buf; }
+    __host__ __device__ static size_t hist(int buf) { return bs(buf) + sizeof(uint32_t) * (size_t)Q * buf; }
+    __host__ __device__ static size_t rs(int buf) { return hist(buf) + sizeof(int) * Q * kHistBins; }
+    __host__ __device__ static size_t kth(int buf) { return rs(buf) + 68 * 4; }        // rs[32], ro[33], pad
+    __host__ __device__ static size_t qpos(int buf) { return kth(buf) + sizeof(T) * Q; }
+    __host__ __device__ static size_t cube(int buf) { return qpos(buf) + sizeof(T) * 3 * Q; }
+    __host__ __device__ static size_t total(int buf)
+    {
+        return (cube(buf) + sizeof(int) * 6 * Q + 15) & ~size_t(15);
+    }
+};
+
+// Is real cell (rx, ry, rz) inside the (periodic) cube c = {lo x3, n x3}?
+__device__ __forceinline__ bool in_cube(const int *c, int rx, int ry, int rz, int G)
 {
-    constexpr int Q = 32 / P;
-    constexpr int TILE = sizeof(T) == 4 ? 128 : 64;
+    return (((rx - c[0]) % G + G) % G) < c[3] && (((ry - c[1]) % G + G) % G) < c[4] &&
+           (((rz - c[2]) % G + G) % G) < c[5];
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
+{
+    using L = WarpSmem<T, P>;
+    constexpr int Q = L::Q;
+    constexpr int TILE = L::TILE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int lane = threadIdx.x & 31;
@@ -227,21 +253,16 @@ __global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
     const uint32_t gmask = (P == 32) ? FULL : (((1u << P) - 1u) << (q * P));
     const uint32_t lt_mask = (1u << lane) - 1u;
 
-    // per-warp shared memory carve-up
-    const size_t bytes_tile = sizeof(Rec<T>) * TILE;
-    const size_t bytes_bd = sizeof(T) * (size_t)Q * a.buf;
-    const size_t bytes_bs = sizeof(uint32_t) * (size_t)Q * a.buf;
-    const size_t bytes_hist = sizeof(int) * Q * kHistBins;
-    const size_t bytes_misc = 68 * 4 + sizeof(T) * Q + 16;
-    const size_t per_warp = (bytes_tile + bytes_bd + bytes_bs + bytes_hist + bytes_misc + 15) & ~size_t(15);
-    unsigned char *wbase = smem_raw + per_warp * wib;
-    Rec<T> *tile = (Rec<T> *)wbase;
-    T *bd = (T *)(wbase + bytes_tile) + (size_t)q * a.buf;
-    uint32_t *bs = (uint32_t *)(wbase + bytes_tile + bytes_bd) + (size_t)q * a.buf;
-    int *hist = (int *)(wbase + bytes_tile + bytes_bd + bytes_bs) + q * kHistBins;
-    uint32_t *rs = (uint32_t *)(wbase + bytes_tile + bytes_bd + bytes_bs + bytes_hist);
+    unsigned char *wbase = smem_raw + L::total(a.buf) * wib;
+    Rec<T> *tile = (Rec<T> *)(wbase + L::tile());
+    T *bd = (T *)(wbase + L::bd()) + (size_t)q * a.buf;
+    uint32_t *bs = (uint32_t *)(wbase + L::bs(a.buf)) + (size_t)q * a.buf;
+    int *hist = (int *)(wbase + L::hist(a.buf)) + q * kHistBins;
+    uint32_t *rs = (uint32_t *)(wbase + L::rs(a.buf));
     uint32_t *ro = rs + 32;     // 33 entries
-    T *kthv = (T *)(ro + 33 + 3) ;
+    T *kthv = (T *)(wbase + L::kth(a.buf));
+    T *qpos = (T *)(wbase + L::qpos(a.buf));      // Q x 3, real coordinates
+    int *cube = (int *)(wbase + L::cube(a.buf));  // Q x 6: lo x3, n x3
 
     const T box = a.box, half = a.half_box, inv_box = a.inv_box;
     const int k = a.k;
@@ -259,19 +280,12 @@ __global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
         const int64_t sq = s_first + (active ? q : 0);
         const typename V4<T>::type qv = a.spos[sq];
         const T rqx = qv.x, rqy = qv.y, rqz = qv.z;
-
-        // bounding box of the chunk (inactive lanes repeat query 0)
-        T blx = rqx, bly = rqy, blz = rqz, bhx = rqx, bhy = rqy, bhz = rqz;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            blx = min(blx, __shfl_xor_sync(FULL, blx, o));
-            bly = min(bly, __shfl_xor_sync(FULL, bly, o));
-            blz = min(blz, __shfl_xor_sync(FULL, blz, o));
-            bhx = max(bhx, __shfl_xor_sync(FULL, bhx, o));
-            bhy = max(bhy, __shfl_xor_sync(FULL, bhy, o));
-            bhz = max(bhz, __shfl_xor_sync(FULL, bhz, o));
+        if (p == 0) {
+            qpos[3 * q] = rqx;
+            qpos[3 * q + 1] = rqy;
+            qpos[3 * q + 2] = rqz;
         }
-        const T ext_b = max(bhx - blx, max(bhy - bly, bhz - blz));
+        __syncwarp();
 
         T R = a.chunk_r ? (T)a.chunk_r[ch] : (T)a.plain_r;
         if (!(R > T(0))) R = box * T(1e-6);
@@ -282,182 +296,217 @@ __global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
 
         while (!certified) {
             ++search_acc;
-            // ---------------- search region for this radius
-            const T lox = blx - R, loy = bly - R, loz = blz - R;
-            const T hix = bhx + R, hiy = bhy + R, hiz = bhz + R;
-            const bool wx = lox < T(0) || hix >= box;
-            const bool wy = loy < T(0) || hiy >= box;
-            const bool wz = loz < T(0) || hiz >= box;
-            bool full = (ext_b + T(2) * R) >= half;
-            if (!full) {
-                if (wx && ((blx < half) != (bhx < half))) full = true;
-                if (wy && ((bly < half) != (bhy < half))) full = true;
-                if (wz && ((blz < half) != (bhz < half))) full = true;
-            }
-            // query and bbox in the warp's frame
-            const T qx = (wx && rqx >= half) ? rqx - box : rqx;
-            const T qy = (wy && rqy >= half) ? rqy - box : rqy;
-            const T qz = (wz && rqz >= half) ? rqz - box : rqz;
-            const T fblx = (wx && blx >= half) ? blx - box : blx;
-            const T fbhx = (wx && bhx >= half) ? bhx - box : bhx;
-            const T fbly = (wy && bly >= half) ? bly - box : bly;
-            const T fbhy = (wy && bhy >= half) ? bhy - box : bhy;
-            const T fblz = (wz && blz >= half) ? blz - box : blz;
-            const T fbhz = (wz && bhz >= half) ? bhz - box : bhz;
+            // ---------------- search region for this radius: the cells of
+            // the chosen level within R of some query of the chunk
+            const bool full = T(2) * R >= half;
+            const bool wx = __any_sync(FULL, rqx - R < T(0) || rqx + R >= box);
+            const bool wy = __any_sync(FULL, rqy - R < T(0) || rqy + R >= box);
+            const bool wz = __any_sync(FULL, rqz - R < T(0) || rqz + R >= box);
+            // the warp's frame (x >= L/2 -> x - L on axes where some query's
+            // region crosses a face) keeps every in-range difference exact
+            // unless another query's region crosses L/2 on such an axis; then
+            // (and for whole-box scans) each pair takes its own minimum image
+            const bool mixed =
+                (wx && __any_sync(FULL, rqx - R < half && half <= rqx + R)) ||
+                (wy && __any_sync(FULL, rqy - R < half && half <= rqy + R)) ||
+                (wz && __any_sync(FULL, rqz - R < half && half <= rqz + R));
+            const bool pairwrap = full || mixed;
+            const T qx = (!pairwrap && wx && rqx >= half) ? rqx - box : rqx;
+            const T qy = (!pairwrap && wy && rqy >= half) ? rqy - box : rqy;
+            const T qz = (!pairwrap && wz && rqz >= half) ? rqz - box : rqz;
 
             tau = full ? T(INFINITY) : R * R;
             cnt = 0;
 
-            // level of the scanned cells: cell side >= R / cpr and >= (extent)/8
-            int l = 16, G = 1 << 16;
-            int c0x = 0, c0y = 0, c0z = 0, nx = 1, ny = 1, nz = 1;
+            int l = 1, G = 2;
             if (!full) {
-                T want = max(R / (T)a.cpr, (ext_b + T(2) * R) * T(0.125));
-                T cells = box / want;   // >= 2^l
-                l = 1;
+                const T cells = box * (T)a.cpr / R;   // 2^l <= cells: side >= R / cpr
                 while (l < kMaxLevel && (T)(1 << (l + 1)) <= cells) ++l;
                 G = 1 << l;
-                const T sc = inv_box * (T)G;
-                c0x = (int)floor(lox * sc); c0y = (int)floor(loy * sc); c0z = (int)floor(loz * sc);
-                nx = (int)floor(hix * sc) - c0x + 1;
-                ny = (int)floor(hiy * sc) - c0y + 1;
-                nz = (int)floor(hiz * sc) - c0z + 1;
-                nx = min(nx, G); ny = min(ny, G); nz = min(nz, G);
             }
-            const int ncells = full ? 1 : nx * ny * nz;
+            const T sc = inv_box * (T)G;
             const T csz = box / (T)G;
+            const T hcs = T(0.5) * csz;
             const T R2c = R * R * T(1.00001) + box * box * T(1e-12);
+            // this query's cube of cells (unwrapped indices) and the warp's bounding cube
+            const int qlx = (int)floor((rqx - R) * sc), qhx = (int)floor((rqx + R) * sc);
+            const int qly = (int)floor((rqy - R) * sc), qhy = (int)floor((rqy + R) * sc);
+            const int qlz = (int)floor((rqz - R) * sc), qhz = (int)floor((rqz + R) * sc);
+            int blx = qlx, bly = qly, blz = qlz, bhx = qhx, bhy = qhy, bhz = qhz;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                blx = min(blx, __shfl_xor_sync(FULL, blx, o));
+                bly = min(bly, __shfl_xor_sync(FULL, bly, o));
+                blz = min(blz, __shfl_xor_sync(FULL, blz, o));
+                bhx = max(bhx, __shfl_xor_sync(FULL, bhx, o));
+                bhy = max(bhy, __shfl_xor_sync(FULL, bhy, o));
+                bhz = max(bhz, __shfl_xor_sync(FULL, bhz, o));
+            }
+            const int64_t nbx = bhx - blx + 1, nby = bhy - bly + 1, nbz = bhz - blz + 1;
+            const bool one = nbx <= G && nby <= G && nbz <= G && nbx * nby * nbz <= 1024;
+            __syncwarp();
+            if (p == 0) {
+                int *cq = cube + 6 * q;
+                cq[0] = qlx; cq[1] = qly; cq[2] = qlz;
+                cq[3] = min(qhx - qlx + 1, G); cq[4] = min(qhy - qly + 1, G); cq[5] = min(qhz - qlz + 1, G);
+            }
+            __syncwarp();
+            const int ncubes = (full || one) ? 1 : nq;
 
-            for (int cb = 0; cb < ncells; cb += 32) {
-                // --------- one batch of up to 32 cells: ranges and prefix
-                uint32_t ra = 0, rb = 0;
-                const int ci = cb + lane;
-                if (full) {
-                    if (lane == 0) { ra = 0; rb = (uint32_t)a.n; }
-                } else if (ci < ncells) {
-                    const int ix = c0x + ci % nx, iy = c0y + (ci / nx) % ny, iz = c0z + ci / (nx * ny);
-                    const int rx = ((ix % G) + G) % G, ry = ((iy % G) + G) % G, rz = ((iz % G) + G) % G;
-                    T flx = (T)rx * csz, fly = (T)ry * csz, flz = (T)rz * csz;
-                    if (wx && rx >= (G >> 1)) flx -= box;
-                    if (wy && ry >= (G >> 1)) fly -= box;
-                    if (wz && rz >= (G >> 1)) flz -= box;
-                    T gx = max(T(0), max(flx - fbhx, fblx - (flx + csz)));
-                    T gy = max(T(0), max(fly - fbhy, fbly - (fly + csz)));
-                    T gz = max(T(0), max(flz - fbhz, fblz - (flz + csz)));
-                    if (gx * gx + gy * gy + gz * gz <= R2c) {
-                        const uint64_t code = morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz);
-                        cell_range(a.cellT, a.keys, a.level_dense, l, code, ra, rb);
+            for (int cc = 0; cc < ncubes; ++cc) {
+                int c0x = 0, c0y = 0, c0z = 0, nx = 1, ny = 1, nz = 1;
+                if (!full) {
+                    if (one) {
+                        c0x = blx; c0y = bly; c0z = blz;
+                        nx = (int)nbx; ny = (int)nby; nz = (int)nbz;
+                    } else {
+                        const int *cq = cube + 6 * cc;
+                        c0x = cq[0]; c0y = cq[1]; c0z = cq[2];
+                        nx = cq[3]; ny = cq[4]; nz = cq[5];
                     }
                 }
-                uint32_t len = rb - ra, inc = len;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    uint32_t y = __shfl_up_sync(FULL, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                const uint32_t total = __shfl_sync(FULL, inc, 31);
-                __syncwarp();
-                rs[lane] = ra;
-                ro[lane] = inc - len;
-                if (lane == 31) ro[32] = inc;
-                __syncwarp();
-
-                for (uint32_t t0 = 0; t0 < total; t0 += TILE) {
-                    const int m = (int)min((uint32_t)TILE, total - t0);
-                    // --------- stage candidates
-                    for (int e = lane; e < m; e += 32) {
-                        const uint32_t g = t0 + (uint32_t)e;
-                        int r = 0;
-#pragma unroll
-                        for (int st = 16; st > 0; st >>= 1)
-                            if (ro[r + st] <= g) r += st;
-                        const uint32_t sidx = rs[r] + (g - ro[r]);
-                        const typename V4<T>::type v = a.spos[sidx];
-                        Rec<T> rec;
-                        if (full) {
-                            rec.x = v.x; rec.y = v.y; rec.z = v.z;
-                        } else {
-                            rec.x = (wx && v.x >= half) ? v.x - box : v.x;
-                            rec.y = (wy && v.y >= half) ? v.y - box : v.y;
-                            rec.z = (wz && v.z >= half) ? v.z - box : v.z;
+                const int ncells = full ? 1 : nx * ny * nz;
+                for (int cb = 0; cb < ncells; cb += 32) {
+                    // --------- one batch of up to 32 cells: ranges and prefix
+                    uint32_t ra = 0, rb = 0;
+                    const int ci = cb + lane;
+                    if (full) {
+                        if (lane == 0) { ra = 0; rb = (uint32_t)a.n; }
+                    } else if (ci < ncells) {
+                        const int ix = c0x + ci % nx, iy = c0y + (ci / nx) % ny, iz = c0z + ci / (nx * ny);
+                        const int rx = ((ix % G) + G) % G, ry = ((iy % G) + G) % G, rz = ((iz % G) + G) % G;
+                        bool keep = true;
+                        for (int c2 = 0; c2 < cc; ++c2)
+                            if (in_cube(cube + 6 * c2, rx, ry, rz, G)) { keep = false; break; }
+                        if (keep) {
+                            // periodic distance from each query to the cell box
+                            keep = false;
+                            const T cx = ((T)rx + T(0.5)) * csz, cy = ((T)ry + T(0.5)) * csz,
+                                    cz = ((T)rz + T(0.5)) * csz;
+                            for (int j = 0; j < nq; ++j) {
+                                T dx = fabs(cx - qpos[3 * j]), dy = fabs(cy - qpos[3 * j + 1]),
+                                  dz = fabs(cz - qpos[3 * j + 2]);
+                                dx = max(T(0), min(dx, box - dx) - hcs);
+                                dy = max(T(0), min(dy, box - dy) - hcs);
+                                dz = max(T(0), min(dz, box - dz) - hcs);
+                                if (dx * dx + dy * dy + dz * dz <= R2c) { keep = true; break; }
+                            }
                         }
-                        rec.s = sidx;
-                        tile[e] = rec;
+                        if (keep) {
+                            const uint64_t code = morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz);
+                            cell_range(a.cellT, a.keys, a.level_dense, l, code, ra, rb);
+                        }
                     }
+                    uint32_t len = rb - ra, inc = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        uint32_t y = __shfl_up_sync(FULL, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    const uint32_t total = __shfl_sync(FULL, inc, 31);
                     __syncwarp();
-                    cand_acc += (unsigned long long)m * (unsigned long long)nq;
-                    // --------- test staged candidates
-                    const int iters = (m + P - 1) / P;
-                    for (int it = 0; it < iters; ++it) {
-                        const int j = it * P + p;
-                        bool pass = false;
-                        T d2 = T(0);
-                        uint32_t sj = 0;
-                        if (j < m && active) {
-                            const Rec<T> c = tile[j];
-                            T dx, dy, dz;
-                            if (full) {
-                                dx = wrapdiff(c.x, rqx, box, half);
-                                dy = wrapdiff(c.y, rqy, box, half);
-                                dz = wrapdiff(c.z, rqz, box, half);
+                    rs[lane] = ra;
+                    ro[lane] = inc - len;
+                    if (lane == 31) ro[32] = inc;
+                    __syncwarp();
+
+                    for (uint32_t t0 = 0; t0 < total; t0 += TILE) {
+                        const int m = (int)min((uint32_t)TILE, total - t0);
+                        // --------- stage candidates
+                        for (int e = lane; e < m; e += 32) {
+                            const uint32_t g = t0 + (uint32_t)e;
+                            int r = 0;
+#pragma unroll
+                            for (int st = 16; st > 0; st >>= 1)
+                                if (ro[r + st] <= g) r += st;
+                            const uint32_t sidx = rs[r] + (g - ro[r]);
+                            const typename V4<T>::type v = a.spos[sidx];
+                            Rec<T> rec;
+                            if (pairwrap) {
+                                rec.x = v.x; rec.y = v.y; rec.z = v.z;
                             } else {
-                                dx = c.x - qx; dy = c.y - qy; dz = c.z - qz;
+                                rec.x = (wx && v.x >= half) ? v.x - box : v.x;
+                                rec.y = (wy && v.y >= half) ? v.y - box : v.y;
+                                rec.z = (wz && v.z >= half) ? v.z - box : v.z;
                             }
-                            d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                            sj = c.s;
-                            pass = d2 <= tau;
+                            rec.s = sidx;
+                            tile[e] = rec;
                         }
-                        const uint32_t bal = __ballot_sync(FULL, pass);
-                        if (pass) {
-                            const int pos = cnt + __popc(bal & gmask & lt_mask);
-                            bd[pos] = d2;
-                            bs[pos] = sj;
-                        }
-                        cnt += __popc(bal & gmask);
-                        // --------- compaction when a buffer fills up
-                        if (((it & 3) == 3 || it == iters - 1) && __any_sync(FULL, cnt > a.cap)) {
-                            if (cnt > a.cap) {
-                                int tb, bk, bo, below_k, upto_k;
-                                group_hist<T, P>(bd, cnt, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
-                                // the bin edge shrinks the buffer only if the k-th entry's bin
-                                // is not crowded (candidates in a distant dense clump can share
-                                // one bin); otherwise cut at the exact k-th value
-                                T ntau = (bk < kHistBins - 1 && upto_k <= a.cap - 4 * P)
-                                             ? bin_upper(tau, tb, bk) : T(-1);
-                                if (!(ntau >= T(0))) {
-                                    group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
-                                    ntau = kthv[q];
-                                    __syncwarp(gmask);
+                        __syncwarp();
+                        cand_acc += (unsigned long long)m * (unsigned long long)nq;
+                        // --------- test staged candidates
+                        const int iters = (m + P - 1) / P;
+                        for (int it = 0; it < iters; ++it) {
+                            const int j = it * P + p;
+                            bool pass = false;
+                            T d2 = T(0);
+                            uint32_t sj = 0;
+                            if (j < m && active) {
+                                const Rec<T> c = tile[j];
+                                T dx, dy, dz;
+                                if (pairwrap) {
+                                    dx = wrapdiff(c.x, rqx, box, half);
+                                    dy = wrapdiff(c.y, rqy, box, half);
+                                    dz = wrapdiff(c.z, rqz, box, half);
+                                } else {
+                                    dx = c.x - qx; dy = c.y - qy; dz = c.z - qz;
                                 }
-                                // order-preserving in-place compaction, P entries per round
-                                int wp = 0;
-                                for (int base = 0; base < cnt; base += P) {
-                                    const int e = base + p;
-                                    T v = T(0);
-                                    uint32_t sv = 0;
-                                    bool keep = false;
-                                    if (e < cnt) { v = bd[e]; sv = bs[e]; keep = v <= ntau; }
-                                    const uint32_t kb = __ballot_sync(gmask, keep);
-                                    __syncwarp(gmask);
-                                    if (keep) {
-                                        const int dst = wp + __popc(kb & lt_mask);
-                                        bd[dst] = v;
-                                        bs[dst] = sv;
-                                    }
-                                    wp += __popc(kb);
-                                    __syncwarp(gmask);
-                                }
-                                cnt = wp;
-                                tau = ntau;
+                                d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                                sj = c.s;
+                                pass = d2 <= tau;
+                            }
+                            const uint32_t bal = __ballot_sync(FULL, pass);
+                            if (pass) {
+                                const int pos = cnt + __popc(bal & gmask & lt_mask);
+                                bd[pos] = d2;
+                                bs[pos] = sj;
+                            }
+                            cnt += __popc(bal & gmask);
+                            // --------- compaction when a buffer fills up
+                            if (((it & 3) == 3 || it == iters - 1) && __any_sync(FULL, cnt > a.cap)) {
                                 if (cnt > a.cap) {
-                                    if (p == 0) atomicOr(a.err, kErrDegenerate);
-                                    cnt = a.cap;
+                                    int tb, bk, bo, below_k, upto_k;
+                                    group_hist<T, P>(bd, cnt, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
+                                    // the bin edge shrinks the buffer only if the k-th entry's bin
+                                    // is not crowded (candidates in a distant dense clump can share
+                                    // one bin); otherwise cut at the exact k-th value
+                                    T ntau = (bk < kHistBins - 1 && upto_k <= a.cap - 4 * P)
+                                                 ? bin_upper(tau, tb, bk) : T(-1);
+                                    if (!(ntau >= T(0))) {
+                                        group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
+                                        ntau = kthv[q];
+                                        __syncwarp(gmask);
+                                    }
+                                    // order-preserving in-place compaction, P entries per round
+                                    int wp = 0;
+                                    for (int base = 0; base < cnt; base += P) {
+                                        const int e = base + p;
+                                        T v = T(0);
+                                        uint32_t sv = 0;
+                                        bool keep = false;
+                                        if (e < cnt) { v = bd[e]; sv = bs[e]; keep = v <= ntau; }
+                                        const uint32_t kb = __ballot_sync(gmask, keep);
+                                        __syncwarp(gmask);
+                                        if (keep) {
+                                            const int dst = wp + __popc(kb & lt_mask);
+                                            bd[dst] = v;
+                                            bs[dst] = sv;
+                                        }
+                                        wp += __popc(kb);
+                                        __syncwarp(gmask);
+                                    }
+                                    cnt = wp;
+                                    tau = ntau;
+                                    if (cnt > a.cap) {
+                                        if (p == 0) atomicOr(a.err, kErrDegenerate);
+                                        cnt = a.cap;
+                                    }
                                 }
+                                __syncwarp();
                             }
-                            __syncwarp();
                         }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
             }
             // ---------------- certification
@@ -546,14 +595,7 @@ __global__ void __launch_bounds__(kKnnThreads) knn_kernel(KnnDev<T> a)
     }
 }
 
-template <typename T, int P> size_t knn_smem_per_warp(int buf)
-{
-    constexpr int Q = 32 / P;
-    constexpr int TILE = sizeof(T) == 4 ? 128 : 64;
-    size_t b = sizeof(Rec<T>) * TILE + sizeof(T) * (size_t)Q * buf + sizeof(uint32_t) * (size_t)Q * buf +
-               sizeof(int) * Q * kHistBins + 68 * 4 + sizeof(T) * Q + 16;
-    return (b + 15) & ~size_t(15);
-}
+template <typename T, int P> size_t knn_smem_per_warp(int buf) { return WarpSmem<T, P>::total(buf); }
 
 template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
 {
