@@ -63,7 +63,7 @@ enum {
 
 typedef struct hop_params {
     int32_t n_dens;       /* Ndens: list length incl. self (Sec. 2); 2..128        */
-    int32_t n_hop;        /* Nhop: hop candidates, 1..n_dens and <= 32              */
+    int32_t n_hop;        /* Nhop: hop candidates, 1..n_dens                         */
     int32_t n_merge;      /* Nmerge: boundary search, 1..n_hop                      */
     float delta_outer;    /* delta_outer: no halo below it (Sec. 2, step 1)         */
     float delta_saddle;   /* delta_saddle: proto-halo merge threshold (step 4)      */
@@ -92,8 +92,8 @@ int hop_set_stream(hop_ctx *ctx, void *cuda_stream);
 /* Message of the last failure on this context ("" when none).  The string
  * lives until the next call on the context. */
 const char *hop_last_error(const hop_ctx *ctx);
-/* Sets the queries per warp of the kNN search (4, 8, 16 or 32) and the
- * number of search cells per radius (1 or 2); 0 keeps the current value.
+/* Sets the queries per warp of the kNN search (1, 2, 4, 8, 16 or 32) and
+ * the number of search cells per radius (1 to 4); 0 keeps the current value.
  * Results do not depend on these; only speed does. */
 int hop_set_tuning(hop_ctx *ctx, int32_t queries_per_warp, int32_t cells_per_radius);
 

@@ -273,9 +273,9 @@ const char *hop_last_error(const hop_ctx *c) { return c ? c->err.c_str() : "null
 int hop_set_tuning(hop_ctx *c, int32_t qpw, int32_t cpr)
 {
     if (!c) return HOP_EINVAL;
-    if (qpw != 0 && qpw != 4 && qpw != 8 && qpw != 16 && qpw != 32)
-        return ctx_fail(c, HOP_EINVAL, "queries per warp must be 4, 8, 16 or 32");
-    if (cpr != 0 && cpr != 1 && cpr != 2) return ctx_fail(c, HOP_EINVAL, "cells per radius must be 1 or 2");
+    if (qpw != 0 && qpw != 1 && qpw != 2 && qpw != 4 && qpw != 8 && qpw != 16 && qpw != 32)
+        return ctx_fail(c, HOP_EINVAL, "queries per warp must be 1, 2, 4, 8, 16 or 32");
+    if (cpr < 0 || cpr > 4) return ctx_fail(c, HOP_EINVAL, "cells per radius must be 1 to 4");
     if (qpw) c->qpw = qpw;
     if (cpr) c->cpr = cpr;
     return HOP_OK;

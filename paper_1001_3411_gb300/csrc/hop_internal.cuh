@@ -14,7 +14,7 @@
 // Morton keys hold 16 bits per axis (48-bit keys): levels 0..16 of the
 // octree over the box; level l has 2^l cells per axis.
 constexpr int kMaxLevel = 16;
-constexpr int kMaxDens = 128;    // Ndens limit (search buffer is 2 * Ndens + slack)
+constexpr int kMaxDens = 128;    // Ndens limit (search buffer is 4 * Ndens + slack)
 constexpr int kHistBins = 32;    // 1/8-octave bins of d^2 used for selection
 
 // Device error word bits (atomicOr'ed by kernels, read by the host).

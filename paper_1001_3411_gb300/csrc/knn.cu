@@ -4,17 +4,18 @@
 // Layout.  Particles are sorted by a 48-bit Morton key, so every octree
 // cell at every level 0..16 is one contiguous range of the sorted float4
 // array {x, y, z, original index}.  A dense table gives the ranges of the
-// cells at one level (about 8 particles per cell); deeper cells are found by
+// cells at one level (about one particle per cell); deeper cells are found by
 // binary search of the keys inside their dense ancestor.
 //
 // Work unit.  One warp takes Q = 32/P consecutive sorted particles (a chunk)
-// and serves them with P lanes each.  The warp scans every cell (at a level
-// matched to the search radius R) that meets the chunk's bounding box
-// dilated by R; candidates are staged in shared memory and each lane tests
-// every P-th staged candidate against its query.
+// and serves them with P lanes each.  For a search radius R the warp scans
+// the cells (side >= R / cpr) lying within R of at least one of its queries;
+// candidates are staged in shared memory (the next tile's loads are issued
+// while the current tile is tested) and each lane tests every P-th staged
+// candidate against its query.
 //
 // Selection.  A query keeps, in shared memory, every candidate seen so far
-// with d^2 <= tau (tau starts at R^2).  When the buffer passes 2 Ndens the
+// with d^2 <= tau (tau starts at R^2).  When the buffer passes 4 Ndens the
 // entries are histogrammed in 1/8-octave bins of d^2 below tau and tau drops
 // to the upper edge of the bin holding the Ndens-th entry, so tau stays an
 // upper bound of the Ndens-th distance of the candidates seen.  The search
@@ -97,59 +98,200 @@ template <typename T> __device__ __forceinline__ T m4(T q)
     return T(0);
 }
 
-// Group (P lanes of one query) histogram of the buffer in 1/8-octave bins
-// below the buffer's largest entry; when the k-th entry falls below the
-// 31 bins the window moves down.  Returns bk (bin of the k-th entry), bo
-// (bin of the n_out-th entry), the count below bk and the window base tb.
+constexpr int KCAP = 32;   // entries of the k-th entry's bin ranked exactly in a small list
+constexpr int OCAP = 64;   // candidates for the n_out nearest ranked in a small list
+
+__device__ __forceinline__ int warp_max_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+template <typename T, int P> __device__ __forceinline__ T group_max(T v)
+{
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// The selection helpers below are called by all 32 lanes of the warp with
+// warp-uniform loop bounds (the largest buffer in the warp); `need` masks
+// the query groups they act for.  Every group then runs the same
+// instruction stream instead of its own data-dependent loops one after the
+// other.
+
+// Histogram of each needing group's buffer in 1/8-octave bins of d^2 below
+// its largest entry; when the k-th (or n_out-th) entry falls in the lowest,
+// open-ended bin the window moves 31 bins down.  Returns bk / bo (bins of
+// the k-th and n_out-th entries), the entries below bk and up to bk, and
+// the window base tb.
 template <typename T, int P>
-__device__ void group_hist(const T *bd, int cnt, int *hist, int k, int n_out, int p,
-                           uint32_t gmask, int &tb, int &bk, int &bo, int &below_k, int &upto_k)
+__device__ void warp_hist(bool need, const T *bd, int cnt, int cmax, int *hist, int k, int n_out,
+                          int p, uint32_t gmask, int &tb, int &bk, int &bo, int &below_k, int &upto_k)
 {
     T vmax = T(0);
-    for (int e = p; e < cnt; e += P) vmax = max(vmax, bd[e]);
-#pragma unroll
-    for (int o = 1; o < P; o <<= 1) vmax = max(vmax, __shfl_xor_sync(gmask, vmax, o));
+    for (int e0 = 0; e0 < cmax; e0 += P) {
+        const int e = e0 + p;
+        if (need && e < cnt) vmax = max(vmax, bd[e]);
+    }
+    vmax = group_max<T, P>(vmax);
     tb = bin_base(vmax);
+    bk = bo = kHistBins - 1;
+    below_k = 0;
+    upto_k = cnt;
+    bool pending = need;
     for (int guard = 0; guard < 96; ++guard) {
-        for (int b = p; b < kHistBins; b += P) hist[b] = 0;
-        __syncwarp(gmask);
-        for (int e = p; e < cnt; e += P) atomicAdd(&hist[bin_of(bd[e], tb)], 1);
-        __syncwarp(gmask);
-        int cum = 0;
-        bk = kHistBins - 1; bo = kHistBins - 1; below_k = 0; upto_k = cnt;
-        bool got_o = n_out <= 0;
-        for (int b = 0; b < kHistBins; ++b) {
-            const int h = hist[b];
-            if (!got_o && cum + h >= n_out) { bo = b; got_o = true; }
-            if (cum + h >= k) { bk = b; below_k = cum; upto_k = cum + h; break; }
-            cum += h;
+        if (pending)
+            for (int b = p; b < kHistBins; b += P) hist[b] = 0;
+        __syncwarp();
+        for (int e0 = 0; e0 < cmax; e0 += P) {
+            const int e = e0 + p;
+            if (pending && e < cnt) atomicAdd(&hist[bin_of(bd[e], tb)], 1);
         }
-        __syncwarp(gmask);
-        // bin 0 also holds everything below the window: look lower
-        if ((bk > 0 && bo > 0) || tb <= kHistBins) break;
-        tb -= kHistBins - 1;
+        __syncwarp();
+        {
+            // the group's P lanes each sum kHistBins/P consecutive bins; a
+            // prefix over the group finds the lanes holding the k-th and
+            // n_out-th entries, which then scan their own bins
+            constexpr int PER = kHistBins / P;
+            int mine = 0;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) mine += pending ? hist[p * PER + i] : 0;
+            int incl = mine;
+#pragma unroll
+            for (int o = 1; o < P; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o, P);
+                if (p >= o) incl += y;
+            }
+            const int excl = incl - mine;
+            int fk = -1, fbelow = 0, fupto = 0, fo = -1;
+            if (pending && excl < k && k <= incl) {
+                int cum = excl;
+                for (int i = 0; i < PER; ++i) {
+                    const int h = hist[p * PER + i];
+                    if (cum + h >= k) { fk = p * PER + i; fbelow = cum; fupto = cum + h; break; }
+                    cum += h;
+                }
+            }
+            if (pending && n_out > 0 && excl < n_out && n_out <= incl) {
+                int cum = excl;
+                for (int i = 0; i < PER; ++i) {
+                    const int h = hist[p * PER + i];
+                    if (cum + h >= n_out) { fo = p * PER + i; break; }
+                    cum += h;
+                }
+            }
+            const uint32_t hk = __ballot_sync(FULL, fk >= 0) & gmask;
+            const uint32_t ho = __ballot_sync(FULL, fo >= 0) & gmask;
+            const int lk = hk ? __ffs(hk) - 1 : 0, lo = ho ? __ffs(ho) - 1 : 0;
+            const int gk = __shfl_sync(FULL, fk, lk), gbelow = __shfl_sync(FULL, fbelow, lk),
+                      gupto = __shfl_sync(FULL, fupto, lk), go = __shfl_sync(FULL, fo, lo);
+            if (pending) {
+                bk = hk ? gk : kHistBins - 1;
+                below_k = hk ? gbelow : 0;
+                upto_k = hk ? gupto : cnt;
+                bo = n_out <= 0 ? kHistBins - 1 : (ho ? go : kHistBins - 1);
+            }
+        }
+        __syncwarp();
+        const bool shift = pending && !((bk > 0 && bo > 0) || tb <= kHistBins);
+        if (shift) tb -= kHistBins - 1;
+        pending = shift;
+        if (!__any_sync(FULL, pending)) break;
     }
 }
 
-// Exact k-th smallest value of the buffer, given that it lies in bin bk and
-// below_k entries lie in lower bins; written to *out by the lane that finds it.
+// Exact k-th smallest value of each needing group's buffer, given that it
+// lies in bin bk with below_k smaller entries: the entries of bin bk are
+// gathered into a small list and ranked there (the whole buffer is scanned
+// only when the bin is crowded).  Written to *out.
 template <typename T, int P>
-__device__ void group_kth(const T *bd, int cnt, int tb, int bk, int below_k, int k, int p,
-                          uint32_t gmask, T *out)
+__device__ void warp_kth(bool need, const T *bd, int cnt, int cmax, int tb, int bk, int below_k,
+                         int k, int p, uint32_t gmask, uint32_t lt_mask, T *kd, T *out)
 {
-    for (int e = p; e < cnt; e += P) {
-        const T v = bd[e];
-        if (bin_of(v, tb) != bk) continue;
-        int lt = below_k, le = below_k;
-        for (int f = 0; f < cnt; ++f) {
-            const T u = bd[f];
-            if (bin_of(u, tb) != bk) continue;
-            lt += u < v;
-            le += u <= v;
+    int nk = 0;
+    for (int e0 = 0; e0 < cmax; e0 += P) {
+        const int e = e0 + p;
+        T v = T(0);
+        bool in = false;
+        if (need && e < cnt) {
+            v = bd[e];
+            in = bin_of(v, tb) == bk;
         }
-        if (lt < k && k <= le) *out = v;
+        const uint32_t m = __ballot_sync(FULL, in) & gmask;
+        if (in) {
+            const int pos = nk + __popc(m & lt_mask);
+            if (pos < KCAP) kd[pos] = v;
+        }
+        nk += __popc(m);
     }
-    __syncwarp(gmask);
+    __syncwarp();
+    const bool small = nk <= KCAP;
+    const int nkmax = warp_max_i((need && small) ? nk : 0);
+    for (int e0 = 0; e0 < nkmax; e0 += P) {
+        const int e = e0 + p;
+        const bool mine = need && small && e < nk;
+        const T v = mine ? kd[e] : T(0);
+        int lt = below_k, le = below_k;
+        for (int f = 0; f < nkmax; ++f) {
+            if (f < nk) {
+                const T u = kd[f];
+                lt += u < v;
+                le += u <= v;
+            }
+        }
+        if (mine && lt < k && k <= le) *out = v;
+    }
+    if (__any_sync(FULL, need && !small)) {
+        for (int e0 = 0; e0 < cmax; e0 += P) {
+            const int e = e0 + p;
+            if (need && !small && e < cnt) {
+                const T v = bd[e];
+                if (bin_of(v, tb) == bk) {
+                    int lt = below_k, le = below_k;
+                    for (int f = 0; f < cnt; ++f) {
+                        const T u = bd[f];
+                        if (bin_of(u, tb) != bk) continue;
+                        lt += u < v;
+                        le += u <= v;
+                    }
+                    if (lt < k && k <= le) *out = v;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Keeps each needing group's entries with d^2 <= ntau, in order, in place
+// (P entries per round: every read of a round precedes its writes).
+template <typename T, int P>
+__device__ void warp_compact(bool need, T *bd, uint32_t *bs, int &cnt, int cmax, T ntau, int p,
+                             uint32_t gmask, uint32_t lt_mask)
+{
+    int wp = 0;
+    for (int base = 0; base < cmax; base += P) {
+        const int e = base + p;
+        T v = T(0);
+        uint32_t sv = 0;
+        bool keep = false;
+        if (need && e < cnt) {
+            v = bd[e];
+            sv = bs[e];
+            keep = v <= ntau;
+        }
+        const uint32_t kb = __ballot_sync(FULL, keep) & gmask;
+        __syncwarp();
+        if (keep) {
+            const int dst = wp + __popc(kb & lt_mask);
+            bd[dst] = v;
+            bs[dst] = sv;
+        }
+        wp += __popc(kb);
+        __syncwarp();
+    }
+    if (need) cnt = wp;
 }
 
 template <typename T> struct KnnDev {
@@ -226,9 +368,12 @@ template <typename T, int P> struct WarpSmem {
     __host__ __device__ static size_t kth(int buf) { return rs(buf) + 68 * 4; }        // rs[32], ro[33], pad
     __host__ __device__ static size_t qpos(int buf) { return kth(buf) + sizeof(T) * Q; }
     __host__ __device__ static size_t cube(int buf) { return qpos(buf) + sizeof(T) * 3 * Q; }
+    __host__ __device__ static size_t kd(int buf) { return (cube(buf) + sizeof(int) * 6 * Q + 15) & ~size_t(15); }
+    __host__ __device__ static size_t od(int buf) { return kd(buf) + sizeof(T) * Q * KCAP; }
+    __host__ __device__ static size_t os(int buf) { return od(buf) + sizeof(T) * Q * OCAP; }
     __host__ __device__ static size_t total(int buf)
     {
-        return (cube(buf) + sizeof(int) * 6 * Q + 15) & ~size_t(15);
+        return (os(buf) + sizeof(uint32_t) * Q * OCAP + 15) & ~size_t(15);
     }
 };
 
@@ -240,7 +385,7 @@ __device__ __forceinline__ bool in_cube(const int *c, int rx, int ry, int rz, in
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
+__global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
 {
     using L = WarpSmem<T, P>;
     constexpr int Q = L::Q;
@@ -263,6 +408,9 @@ __global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
     T *kthv = (T *)(wbase + L::kth(a.buf));
     T *qpos = (T *)(wbase + L::qpos(a.buf));      // Q x 3, real coordinates
     int *cube = (int *)(wbase + L::cube(a.buf));  // Q x 6: lo x3, n x3
+    T *kd = (T *)(wbase + L::kd(a.buf)) + q * KCAP;
+    T *od = (T *)(wbase + L::od(a.buf)) + q * OCAP;
+    uint32_t *os = (uint32_t *)(wbase + L::os(a.buf)) + q * OCAP;
 
     const T box = a.box, half = a.half_box, inv_box = a.inv_box;
     const int k = a.k;
@@ -410,17 +558,34 @@ __global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
                     if (lane == 31) ro[32] = inc;
                     __syncwarp();
 
+                    // --------- stream the batch's candidates through the tile.  The
+                    // next tile's global loads are issued before the current tile
+                    // is tested, so their latency overlaps the tests.
+                    constexpr int PER_LANE = TILE / 32;
+                    typename V4<T>::type pv[PER_LANE];
+                    uint32_t pidx[PER_LANE];
+                    int cur = 0;   // range of this lane's next element (moves forward only)
+                    auto fetch = [&](uint32_t t0) {
+#pragma unroll
+                        for (int jj = 0; jj < PER_LANE; ++jj) {
+                            const uint32_t g = t0 + (uint32_t)(lane + 32 * jj);
+                            pidx[jj] = 0xffffffffu;
+                            if (g < total) {
+                                while (ro[cur + 1] <= g) ++cur;
+                                pidx[jj] = rs[cur] + (g - ro[cur]);
+                            }
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < PER_LANE; ++jj)
+                            if (pidx[jj] != 0xffffffffu) pv[jj] = a.spos[pidx[jj]];
+                    };
+                    if (total > 0) fetch(0);
                     for (uint32_t t0 = 0; t0 < total; t0 += TILE) {
                         const int m = (int)min((uint32_t)TILE, total - t0);
-                        // --------- stage candidates
-                        for (int e = lane; e < m; e += 32) {
-                            const uint32_t g = t0 + (uint32_t)e;
-                            int r = 0;
 #pragma unroll
-                            for (int st = 16; st > 0; st >>= 1)
-                                if (ro[r + st] <= g) r += st;
-                            const uint32_t sidx = rs[r] + (g - ro[r]);
-                            const typename V4<T>::type v = a.spos[sidx];
+                        for (int jj = 0; jj < PER_LANE; ++jj) {
+                            if (pidx[jj] == 0xffffffffu) continue;
+                            const typename V4<T>::type v = pv[jj];
                             Rec<T> rec;
                             if (pairwrap) {
                                 rec.x = v.x; rec.y = v.y; rec.z = v.z;
@@ -429,80 +594,86 @@ __global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
                                 rec.y = (wy && v.y >= half) ? v.y - box : v.y;
                                 rec.z = (wz && v.z >= half) ? v.z - box : v.z;
                             }
-                            rec.s = sidx;
-                            tile[e] = rec;
+                            rec.s = pidx[jj];
+                            tile[lane + 32 * jj] = rec;
                         }
                         __syncwarp();
+                        if (t0 + TILE < total) fetch(t0 + TILE);
                         cand_acc += (unsigned long long)m * (unsigned long long)nq;
-                        // --------- test staged candidates
-                        const int iters = (m + P - 1) / P;
-                        for (int it = 0; it < iters; ++it) {
-                            const int j = it * P + p;
-                            bool pass = false;
-                            T d2 = T(0);
-                            uint32_t sj = 0;
-                            if (j < m && active) {
-                                const Rec<T> c = tile[j];
-                                T dx, dy, dz;
-                                if (pairwrap) {
-                                    dx = wrapdiff(c.x, rqx, box, half);
-                                    dy = wrapdiff(c.y, rqy, box, half);
-                                    dz = wrapdiff(c.z, rqz, box, half);
-                                } else {
-                                    dx = c.x - qx; dy = c.y - qy; dz = c.z - qz;
+                        // --------- test staged candidates, 4 per lane per step
+                        constexpr int STEP = 4 * P;
+                        const int steps = (m + STEP - 1) / STEP;
+                        for (int st = 0; st < steps; ++st) {
+                            T d2[4];
+                            uint32_t sj[4];
+                            bool ps[4];
+                            int c = 0;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int j = st * STEP + u * P + p;
+                                ps[u] = false;
+                                d2[u] = T(0);
+                                sj[u] = 0;
+                                if (j < m && active) {
+                                    const Rec<T> cd = tile[j];
+                                    T dx, dy, dz;
+                                    if (pairwrap) {
+                                        dx = wrapdiff(cd.x, rqx, box, half);
+                                        dy = wrapdiff(cd.y, rqy, box, half);
+                                        dz = wrapdiff(cd.z, rqz, box, half);
+                                    } else {
+                                        dx = cd.x - qx; dy = cd.y - qy; dz = cd.z - qz;
+                                    }
+                                    d2[u] = fma(dx, dx, fma(dy, dy, dz * dz));
+                                    sj[u] = cd.s;
+                                    ps[u] = d2[u] <= tau;
                                 }
-                                d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                                sj = c.s;
-                                pass = d2 <= tau;
+                                c += ps[u] ? 1 : 0;
                             }
-                            const uint32_t bal = __ballot_sync(FULL, pass);
-                            if (pass) {
-                                const int pos = cnt + __popc(bal & gmask & lt_mask);
-                                bd[pos] = d2;
-                                bs[pos] = sj;
+                            // positions: exclusive prefix of the pass counts in the group
+                            int incl = c;
+#pragma unroll
+                            for (int o = 1; o < P; o <<= 1) {
+                                const int y = __shfl_up_sync(FULL, incl, o, P);
+                                if (p >= o) incl += y;
                             }
-                            cnt += __popc(bal & gmask);
+                            const int gtot = __shfl_sync(FULL, incl, P - 1, P);
+                            int pos = cnt + incl - c;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (ps[u]) {
+                                    bd[pos] = d2[u];
+                                    bs[pos] = sj[u];
+                                    ++pos;
+                                }
+                            }
+                            cnt += gtot;
                             // --------- compaction when a buffer fills up
-                            if (((it & 3) == 3 || it == iters - 1) && __any_sync(FULL, cnt > a.cap)) {
-                                if (cnt > a.cap) {
-                                    int tb, bk, bo, below_k, upto_k;
-                                    group_hist<T, P>(bd, cnt, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
-                                    // the bin edge shrinks the buffer only if the k-th entry's bin
-                                    // is not crowded (candidates in a distant dense clump can share
-                                    // one bin); otherwise cut at the exact k-th value
-                                    T ntau = (bk < kHistBins - 1 && upto_k <= a.cap - 4 * P)
-                                                 ? bin_upper(tau, tb, bk) : T(-1);
-                                    if (!(ntau >= T(0))) {
-                                        group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
-                                        ntau = kthv[q];
-                                        __syncwarp(gmask);
-                                    }
-                                    // order-preserving in-place compaction, P entries per round
-                                    int wp = 0;
-                                    for (int base = 0; base < cnt; base += P) {
-                                        const int e = base + p;
-                                        T v = T(0);
-                                        uint32_t sv = 0;
-                                        bool keep = false;
-                                        if (e < cnt) { v = bd[e]; sv = bs[e]; keep = v <= ntau; }
-                                        const uint32_t kb = __ballot_sync(gmask, keep);
-                                        __syncwarp(gmask);
-                                        if (keep) {
-                                            const int dst = wp + __popc(kb & lt_mask);
-                                            bd[dst] = v;
-                                            bs[dst] = sv;
-                                        }
-                                        wp += __popc(kb);
-                                        __syncwarp(gmask);
-                                    }
-                                    cnt = wp;
+                            if (__any_sync(FULL, cnt > a.cap)) {
+                                const bool need = cnt > a.cap;
+                                const int cmax = warp_max_i(cnt);
+                                int tb, bk, bo, below_k, upto_k;
+                                warp_hist<T, P>(need, bd, cnt, cmax, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
+                                // the bin edge shrinks the buffer only if the k-th entry's bin
+                                // is not crowded (candidates in a distant dense clump can share
+                                // one bin); otherwise cut at the exact k-th value
+                                T ntau = (need && bk < kHistBins - 1 && upto_k <= a.cap - 4 * P)
+                                             ? bin_upper(tau, tb, bk) : T(-1);
+                                const bool exact = need && !(ntau >= T(0));
+                                if (__any_sync(FULL, exact)) {
+                                    warp_kth<T, P>(exact, bd, cnt, cmax, tb, bk, below_k, k, p, gmask, lt_mask,
+                                                   kd, &kthv[q]);
+                                    if (exact) ntau = kthv[q];
+                                    __syncwarp();
+                                }
+                                warp_compact<T, P>(need, bd, bs, cnt, cmax, ntau, p, gmask, lt_mask);
+                                if (need) {
                                     tau = ntau;
                                     if (cnt > a.cap) {
                                         if (p == 0) atomicOr(a.err, kErrDegenerate);
                                         cnt = a.cap;
                                     }
                                 }
-                                __syncwarp();
                             }
                         }
                         __syncwarp();
@@ -531,19 +702,22 @@ __global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
         }
         if (!certified) continue;
 
-        // -------------------- selection (per query group)
-        if (active) {
-            const int n_out = a.n_out;
+        // -------------------- selection (all lanes, per query group)
+        {
+            const bool need = active;
+            const int n_out = (a.nbr_s != nullptr) ? a.n_out : 0;
+            const int cmax = warp_max_i(cnt);
             int tb, bk, bo, below_k, upto_k;
-            group_hist<T, P>(bd, cnt, hist, k, n_out, p, gmask, tb, bk, bo, below_k, upto_k);
-            group_kth<T, P>(bd, cnt, tb, bk, below_k, k, p, gmask, &kthv[q]);
+            warp_hist<T, P>(need, bd, cnt, cmax, hist, k, n_out, p, gmask, tb, bk, bo, below_k, upto_k);
+            warp_kth<T, P>(need, bd, cnt, cmax, tb, bk, below_k, k, p, gmask, lt_mask, kd, &kthv[q]);
             const T vk = kthv[q];
             // density: fixed-point sum of w(2 r / r_k) over entries with d^2 < r_k^2
             unsigned long long wsum = 0;
             const T rk = sqrt(vk);
-            if (vk > T(0)) {
-                const T inv_h = T(2) / rk;
-                for (int e = p; e < cnt; e += P) {
+            const T inv_h = vk > T(0) ? T(2) / rk : T(0);
+            for (int e0 = 0; e0 < cmax; e0 += P) {
+                const int e = e0 + p;
+                if (need && e < cnt) {
                     const T v = bd[e];
                     if (v < vk) {
                         const T w = m4<T>(sqrt(v) * inv_h);
@@ -552,28 +726,70 @@ __global__ void __launch_bounds__(kKnnThreads, 1) knn_kernel(KnnDev<T> a)
                 }
             }
 #pragma unroll
-            for (int o = 1; o < P; o <<= 1) wsum += __shfl_xor_sync(gmask, wsum, o);
-            // the n_out nearest in (d^2, original index) order
-            if (n_out > 0 && a.nbr_s) {
-                for (int e = p; e < cnt; e += P) {
-                    const T v = bd[e];
-                    if (bin_of(v, tb) > bo) continue;
-                    const uint32_t se = bs[e];
+            for (int o = 1; o < P; o <<= 1) wsum += __shfl_xor_sync(FULL, wsum, o);
+            // the n_out nearest in (d^2, original index) order, ranked in a
+            // small list of the entries up to the n_out-th entry's bin
+            if (n_out > 0) {
+                int no = 0;
+                for (int e0 = 0; e0 < cmax; e0 += P) {
+                    const int e = e0 + p;
+                    T v = T(0);
+                    bool in = false;
+                    if (need && e < cnt) {
+                        v = bd[e];
+                        in = bin_of(v, tb) <= bo;
+                    }
+                    const uint32_t m = __ballot_sync(FULL, in) & gmask;
+                    if (in) {
+                        const int pos = no + __popc(m & lt_mask);
+                        if (pos < OCAP) { od[pos] = v; os[pos] = bs[e]; }
+                    }
+                    no += __popc(m);
+                }
+                __syncwarp();
+                const bool small = no <= OCAP;
+                const int nomax = warp_max_i((need && small) ? no : 0);
+                for (int e0 = 0; e0 < nomax; e0 += P) {
+                    const int e = e0 + p;
+                    const bool mine = need && small && e < no;
+                    const T v = mine ? od[e] : T(0);
+                    const uint32_t se = mine ? os[e] : 0u;
                     uint32_t oe = 0xffffffffu;
                     int rank = 0;
-                    for (int f = 0; f < cnt; ++f) {
-                        const T u = bd[f];
-                        if (u < v) { ++rank; continue; }
-                        if (u == v && f != e) {
-                            if (oe == 0xffffffffu) oe = orig_of<T>(a.spos[se]);
-                            const uint32_t of = orig_of<T>(a.spos[bs[f]]);
-                            rank += of < oe;
+                    for (int f = 0; f < nomax; ++f) {
+                        if (f < no) {
+                            const T u = od[f];
+                            rank += u < v;
+                            if (mine && u == v && f != e) {
+                                if (oe == 0xffffffffu) oe = orig_of<T>(a.spos[se]);
+                                rank += orig_of<T>(a.spos[os[f]]) < oe;
+                            }
                         }
                     }
-                    if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    if (mine && rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                }
+                if (__any_sync(FULL, need && !small)) {
+                    for (int e0 = 0; e0 < cmax; e0 += P) {
+                        const int e = e0 + p;
+                        if (!(need && !small && e < cnt)) continue;
+                        const T v = bd[e];
+                        if (bin_of(v, tb) > bo) continue;
+                        const uint32_t se = bs[e];
+                        uint32_t oe = 0xffffffffu;
+                        int rank = 0;
+                        for (int f = 0; f < cnt; ++f) {
+                            const T u = bd[f];
+                            if (u < v) { ++rank; continue; }
+                            if (u == v && f != e) {
+                                if (oe == 0xffffffffu) oe = orig_of<T>(a.spos[se]);
+                                rank += orig_of<T>(a.spos[bs[f]]) < oe;
+                            }
+                        }
+                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    }
                 }
             }
-            if (p == 0) {
+            if (need && p == 0) {
                 float dens;
                 if (vk > T(0)) {
                     const T h = rk * T(0.5);
@@ -613,7 +829,7 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     d.k = a.k;
     d.n_out = a.n_out;
     d.ld_out = a.ld_out;
-    d.cap = 2 * a.k;
+    d.cap = 4 * a.k;   // room for 4 Ndens entries per query: compactions are rare
     d.buf = d.cap + 4 * P + 4;
     d.chunk_r = a.chunk_r;
     d.plain_r = a.plain_r;
@@ -626,17 +842,25 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     d.chunk_counter = c->d_counters + kCntNum;
     d.err = c->d_err;
     HOP_CUDA(c, cudaMemsetAsync(d.chunk_counter, 0, sizeof(unsigned long long), c->stream));
-    const size_t smem = knn_smem_per_warp<T, P>(d.buf) * kKnnWarps;
+    // as many warps per block (4, 2 or 1) as fit in the opt-in shared memory
+    int max_smem = 0;
+    HOP_CUDA(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const size_t per_warp = knn_smem_per_warp<T, P>(d.buf);
+    int warps = kKnnWarps;
+    while (warps > 1 && per_warp * warps > (size_t)max_smem) warps >>= 1;
+    if (per_warp * warps > (size_t)max_smem)
+        return ctx_fail(c, HOP_EINVAL, "kNN search buffer does not fit in shared memory");
+    const size_t smem = per_warp * warps;
     auto kern = knn_kernel<T, P>;
     HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKnnThreads, smem));
+    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
     if (per_sm < 1) return ctx_fail(c, HOP_EINVAL, "kNN search buffer does not fit in shared memory");
     int64_t blocks = (int64_t)per_sm * c->num_sms;
-    const int64_t need = (d.n_chunks + kKnnWarps - 1) / kKnnWarps;
+    const int64_t need = (d.n_chunks + warps - 1) / warps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kKnnThreads, smem, c->stream>>>(d);
+    kern<<<(unsigned)blocks, warps * 32, smem, c->stream>>>(d);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -646,12 +870,14 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
 int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr)
 {
     if (a.k < 2 || a.k > kMaxDens) return ctx_fail(c, HOP_EINVAL, "n_dens out of range");
-    if (cpr != 1 && cpr != 2) cpr = 1;
+    if (cpr < 1 || cpr > 4) cpr = 1;
     switch (qpw) {
     case 32: return f64 ? knn_run<double, 1>(c, a, cpr) : knn_run<float, 1>(c, a, cpr);
     case 16: return f64 ? knn_run<double, 2>(c, a, cpr) : knn_run<float, 2>(c, a, cpr);
     case 8: return f64 ? knn_run<double, 4>(c, a, cpr) : knn_run<float, 4>(c, a, cpr);
     case 4: return f64 ? knn_run<double, 8>(c, a, cpr) : knn_run<float, 8>(c, a, cpr);
-    default: return ctx_fail(c, HOP_EINVAL, "queries per warp must be 4, 8, 16 or 32");
+    case 2: return f64 ? knn_run<double, 16>(c, a, cpr) : knn_run<float, 16>(c, a, cpr);
+    case 1: return f64 ? knn_run<double, 32>(c, a, cpr) : knn_run<float, 32>(c, a, cpr);
+    default: return ctx_fail(c, HOP_EINVAL, "queries per warp must be 1, 2, 4, 8, 16 or 32");
     }
 }

@@ -158,7 +158,7 @@ def test_radius_policies_give_identical_output(hop, mode):
     assert base["n_groups"] == other["n_groups"]
 
 
-@pytest.mark.parametrize("qpw,cpr", [(4, 1), (16, 2), (32, 1), (8, 2)])
+@pytest.mark.parametrize("qpw,cpr", [(4, 1), (16, 2), (32, 1), (8, 2), (1, 3), (2, 2), (4, 4)])
 def test_tuning_does_not_change_results(hop, qpw, cpr):
     pos = synth.nfw_box(40000, 41)[0]
     base = hop.hop_run(_to_dev(pos), _params(), ld_nbr=16)
