@@ -48,7 +48,8 @@ enum {
     HOP_ETABLE = 4,      /* caller's edge capacity too small; *n_edges = required   */
     HOP_ETIMEOUT = 5,    /* a device loop reached its iteration limit               */
     HOP_EDEGENERATE = 6, /* more equidistant neighbours than the search buffer holds */
-    HOP_ENOMODEL = 7     /* learned radius requested but no network is loaded        */
+    HOP_ENOMODEL = 7,    /* learned radius requested but no network is loaded        */
+    HOP_ESTATIC = 8      /* n exceeds the fixed scratch of hop_link_static           */
 };
 
 /* How the kNN search picks each warp's first search radius.  All three give
@@ -173,6 +174,35 @@ int hop_merge(hop_ctx *ctx, const uint32_t *chain, const float *dens, int64_t n,
 int hop_run(hop_ctx *ctx, const void *pos, int64_t n, const hop_params *params,
             float *dens, int32_t *group, int64_t *n_groups,
             uint32_t *nbr, int32_t ld_nbr, uint32_t *chain);
+
+/*
+ * hop_link without any device allocation.  (No counterpart in the paper:
+ * this is an interface for callers, not part of the method.)
+ *
+ * Some callers cannot call cudaMalloc.  For example, a host program may give
+ * all device memory to its own pool allocator and forbid other
+ * allocations.  A latency-bound loop may not afford one either, because a
+ * device allocation can synchronise the device.  Such callers cannot create
+ * a hop_ctx, whose scratch memory grows on demand.  This call computes
+ * exactly what hop_link computes (same hops, same chain labels, same
+ * errors).  It keeps its scratch, the per-particle density keys and an error
+ * word, in one array in this library's own device memory:
+ * HOP_STATIC_LINK_MAX_N * 8 + 256 bytes (8 MiB + 256 B).  Every GPU that
+ * loads the library holds that array until the process exits.
+ *   dens, nbr, ld_nbr, n, n_hop  as in hop_link (device pointers);
+ *   hop, chain  n uint32 each, device, both required;
+ *   cuda_stream  the stream to enqueue on (NULL = legacy default stream).
+ * Returns HOP_ESTATIC without touching any buffer when n > the maximum.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current).  Make that first call before any stream
+ * capture.  The array is shared by every call on a device and keeps the last
+ * call's contents.  Calls that overlap on the GPU (different streams or
+ * threads, not ordered by the caller) race on it and give wrong results.
+ * Like hop_link, the call synchronises the stream to read its error word.
+ */
+#define HOP_STATIC_LINK_MAX_N (1 << 20)
+int hop_link_static(const float *dens, const uint32_t *nbr, int32_t ld_nbr, int64_t n,
+                    int32_t n_hop, uint32_t *hop, uint32_t *chain, void *cuda_stream);
 
 /* Counters and stage times (ms, CUDA events on the context stream) of the
  * last hop_run / hop_density call. */

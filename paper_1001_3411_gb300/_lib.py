@@ -16,17 +16,19 @@ import numpy as np
 from .build import LIB
 
 HOP_OK, HOP_EINVAL, HOP_ENOMEM, HOP_ECUDA, HOP_ETABLE, HOP_ETIMEOUT, HOP_EDEGENERATE, HOP_ENOMODEL = range(8)
+HOP_ESTATIC = 8
+HOP_STATIC_LINK_MAX_N = 1 << 20
 HOP_RADIUS_PLAIN, HOP_RADIUS_COUNT, HOP_RADIUS_LEARNED = 0, 1, 2
 MLP_IN, MLP_HID = 27, 64
 MLP_NPARAM = 64 * 27 + 64 + 64 * 64 + 64 + 64 + 1
 
 ERROR_NAMES = {0: "HOP_OK", 1: "HOP_EINVAL", 2: "HOP_ENOMEM", 3: "HOP_ECUDA", 4: "HOP_ETABLE",
-               5: "HOP_ETIMEOUT", 6: "HOP_EDEGENERATE", 7: "HOP_ENOMODEL"}
+               5: "HOP_ETIMEOUT", 6: "HOP_EDEGENERATE", 7: "HOP_ENOMODEL", 8: "HOP_ESTATIC"}
 
 EXPORTS = ["hop_default_params", "hop_create", "hop_destroy", "hop_set_stream", "hop_last_error",
            "hop_set_tuning", "hop_density", "hop_link", "hop_boundaries", "hop_merge", "hop_run",
            "hop_get_stats", "hop_mlp_load", "hop_mlp_get", "hop_mlp_samples", "hop_mlp_forward",
-           "hop_mlp_grad", "hop_mlp_train"]
+           "hop_mlp_grad", "hop_mlp_train", "hop_link_static"]
 
 
 class HopParams(C.Structure):
@@ -89,6 +91,7 @@ def load_library(path: str = LIB):
             "hop_mlp_forward": (C.c_int, [vp, vp, i64, vp]),
             "hop_mlp_grad": (C.c_int, [vp, vp, vp, i64, C.POINTER(f64), vp]),
             "hop_mlp_train": (C.c_int, [vp, vp, vp, i64, i32, i32, f32, C.c_uint64, C.POINTER(f64)]),
+            "hop_link_static": (C.c_int, [vp, vp, i32, i64, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

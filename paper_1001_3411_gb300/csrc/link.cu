@@ -339,3 +339,78 @@ int scatter_outputs(hop_ctx *c, const uint32_t *perm, int64_t n, const float *de
     HOP_LAUNCH(c);
     return HOP_OK;
 }
+
+// ------------------------------------------------------------------------
+// hop_link_static: hop_link for callers that cannot allocate device memory.
+// Its scratch (density keys, then an error word) lives in this file-scope
+// array instead of a context's buffers.  Host code must not pass the
+// symbol itself to a kernel: on the host it names a stand-in, not device
+// memory.  The device address comes from cudaGetSymbolAddress, looked up
+// once per device with that device current.
+static __device__ __align__(256) unsigned long long g_link_static_scratch[HOP_STATIC_LINK_MAX_N + 32];
+
+#include <mutex>
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kStaticMaxDevices] = {};
+int g_static_sms[kStaticMaxDevices] = {};
+
+// Device address of the scratch array and the SM count of the current device.
+int static_scratch(void **ptr, int *sms)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return HOP_ECUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_link_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HOP_ECUDA;
+        }
+        int s = 0;
+        if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) {
+            cudaGetLastError();
+            return HOP_ECUDA;
+        }
+        g_static_ptr[dev] = p;
+        g_static_sms[dev] = s;
+    }
+    *ptr = g_static_ptr[dev];
+    *sms = g_static_sms[dev];
+    return HOP_OK;
+}
+
+}  // namespace
+
+extern "C" int hop_link_static(const float *dens, const uint32_t *nbr, int32_t ld_nbr, int64_t n,
+                               int32_t n_hop, uint32_t *hop, uint32_t *chain, void *cuda_stream)
+{
+    if (!dens || !nbr || !hop || !chain || n <= 0 || n_hop < 1 || n_hop > ld_nbr) return HOP_EINVAL;
+    if (n > HOP_STATIC_LINK_MAX_N) return HOP_ESTATIC;
+    void *base = nullptr;
+    int sms = 0;
+    int rc = static_scratch(&base, &sms);
+    if (rc) return rc;
+    uint64_t *dkey = (uint64_t *)base;
+    uint32_t *flag = (uint32_t *)(dkey + HOP_STATIC_LINK_MAX_N);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int64_t b = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 32);
+    const int blocks = (int)std::max<int64_t>(b, 1);
+    // the array keeps the previous call's contents: the error word starts at zero
+    if (cudaMemsetAsync(flag, 0, 8, st) != cudaSuccess) return HOP_ECUDA;
+    dkey_kernel<<<blocks, 256, 0, st>>>(dens, nullptr, n, dkey);
+    hop_kernel<<<blocks, 256, 0, st>>>(dkey, nbr, ld_nbr, n, n_hop, hop, chain, flag);
+    chain_halving_kernel<<<blocks, 256, 0, st>>>(chain, n, flag);
+    chain_root_kernel<<<blocks, 256, 0, st>>>(chain, n, flag);
+    chain_check_kernel<<<blocks, 256, 0, st>>>(hop, chain, n, flag);
+    if (cudaGetLastError() != cudaSuccess) return HOP_ECUDA;
+    uint32_t h = 0;
+    if (cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HOP_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HOP_ECUDA;
+    if (h & kErrBadIndex) return HOP_EINVAL;
+    if (h & kErrChainLoop) return HOP_ETIMEOUT;
+    return HOP_OK;
+}
