@@ -29,7 +29,7 @@ def init_params(seed: int = 0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     w1 = rng.normal(0.0, np.sqrt(2.0 / MLP_IN), (MLP_HID, MLP_IN))
     w2 = rng.normal(0.0, np.sqrt(2.0 / MLP_HID), (MLP_HID, MLP_HID))
-    w3 = rng.normal(0.0, np.sqrt(1.0 / MLP_HID), MLP_HID)
+    w3 = rng.normal(0.0, 0.1 * np.sqrt(1.0 / MLP_HID), MLP_HID)   # start near the bias
     p = np.concatenate([w1.ravel(), np.zeros(MLP_HID), w2.ravel(), np.zeros(MLP_HID), w3, [0.0]])
     assert p.size == MLP_NPARAM
     return p.astype(np.float32)
@@ -47,7 +47,6 @@ def train(hop: Hop, feat, target, epochs: int = 8, batch: int = 8192, lr: float 
     """Trains in place on the GPU; returns (params, margin, stats)."""
     import torch
     t0 = time.time()
-    hop.hop_mlp_load(init_params(seed), 0.0)
     # centre the output bias on the target mean so training starts close
     p0 = init_params(seed)
     p0[-1] = float(target.mean())

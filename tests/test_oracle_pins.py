@@ -391,3 +391,46 @@ def test_plummer_isolated_spheres_give_one_halo_each():
     for a, b, s_ in zip(r["lo"], r["hi"], r["s"]):
         if d[a] >= 240.0 and d[b] >= 240.0 and s_ >= 400.0:
             assert g[a] == g[b]
+
+
+# ------------------------------------------------- learned-radius network ---
+
+def test_mlp_oracle_hand_computed_case():
+    """One active path through the network, computed by hand:
+    y = b3 + w3[0] * relu(b2[0] + W2[0,0] * relu(b1[0] + W1[0,2] * x2))."""
+    from oracle import mlp
+    w1 = np.zeros((64, 27)); w1[0, 2] = 0.5
+    b1 = np.zeros(64); b1[0] = -1.0
+    w2 = np.zeros((64, 64)); w2[0, 0] = 3.0
+    b2 = np.zeros(64); b2[0] = 0.25
+    w3 = np.zeros(64); w3[0] = -2.0
+    p = mlp.pack(w1, b1, w2, b2, w3, 0.75)
+    x = np.zeros((3, 27)); x[:, 2] = [4.0, 1.0, 6.0]       # hidden pre-activations 1, -0.5, 2
+    expect = [0.75 - 2.0 * (0.25 + 3.0 * 1.0), 0.75 - 2.0 * 0.25, 0.75 - 2.0 * (0.25 + 3.0 * 2.0)]
+    np.testing.assert_allclose(mlp.forward(p, x), expect, rtol=0, atol=1e-14)
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 0.3, mlp.NPARAM)
+    x = rng.normal(1.0, 1.0, (40, 27))
+    t = rng.normal(0.0, 1.0, 40)
+    _, g = mlp.loss_and_grad(p, x, t)
+    idx = rng.choice(mlp.NPARAM, 60, replace=False)
+    idx = np.concatenate([idx, [mlp.NPARAM - 1, 0, 64 * 27]])   # b3, a W1 weight, b1[0]
+    for i in idx:
+        e = np.zeros(mlp.NPARAM); e[i] = 1e-6
+        fd = (mlp.loss_and_grad(p + e, x, t)[0] - mlp.loss_and_grad(p - e, x, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(g[i]), (i, fd, g[i])
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    from oracle import mlp
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7, 1.0 + 3 * 2 ** -8, -2.5, 1e-3], dtype=np.float32)
+    got = mlp.bf16_round(vals)
+    # 1 + 2^-8 is half way between 1 and 1 + 2^-7: ties go to the even mantissa (1)
+    assert got[0] == 1.0 and got[1] == 1.0 and got[2] == 1.0 + 2 ** -7
+    assert got[3] == 1.0 + 2 * 2 ** -7          # 1 + 3*2^-8: tie to even goes up
+    assert got[4] == -2.5
+    assert abs(got[5] - 1e-3) / 1e-3 < 2 ** -8
