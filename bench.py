@@ -100,6 +100,25 @@ def gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+def knn_traffic_per_particle():
+    """DRAM bytes per particle of the kNN kernel from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "knn_kernel_nfw16M_learned.md")).read()
+        src = open(os.path.join(ROOT, "paper_1001_3411_gb300", "csrc", "knn.cu"), "rb").read()
+    except OSError:
+        return None, "no capture"
+    want = re.search(r"knn_source_sha256_16: ([0-9a-f]+)", txt)
+    per = re.search(r"traffic_bytes_per_particle: ([0-9.]+)", txt)
+    if not want or not per:
+        return None, "no capture"
+    if hashlib.sha256(src).hexdigest()[:16] != want.group(1):
+        return None, "kernel changed since the ncu capture"
+    return float(per.group(1)), "ncu dram__bytes_read+write on the 16.8M-particle case, scaled by particles"
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -323,6 +342,7 @@ def run_gb300(args):
     fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s at the sampled clock
     alg_flop = n * IDEAL_CANDIDATES * FLOP_PER_CANDIDATE
     achieved = alg_flop / (knn_ms * 1e-3) / 1e12
+    tpp, tsrc = knn_traffic_per_particle()
 
     def stage(st):
         keys = ("ms_sort", "ms_radius", "ms_knn", "ms_link", "ms_boundaries", "ms_merge", "ms_total")
@@ -361,7 +381,8 @@ def run_gb300(args):
         "speedup_learned_vs_plain": ms_p / ms_l,
         "roofline": {"kernel": "knn_kernel<float,P> (kNN + M4 density)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": (tpp * n if tpp else None),
+                     "traffic_basis": tsrc,
                      "basis": ("algorithmic flop = N x 64 x 6/pi candidates x 8 flop; peak = SMs x 128 "
                                "FP32 lanes x 2 x sampled median SM clock"),
                      "knn_ms": knn_ms},

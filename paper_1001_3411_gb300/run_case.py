@@ -1,0 +1,51 @@
+"""Runs HOP on one synthetic box a few times and prints each call's stage
+times and counters: a small driver for profilers (ncu) and quick timing.
+
+  python -m paper_1001_3411_gb300.run_case --n 16777216 --radius learned \
+      --qpw 4 --cpr 1 --steps 2
+
+The box is the NFW + 40% background generator with the 512^3 workload's
+seed (``synth.nfw_box``), so any --n is a smaller copy of the benchmark box.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+
+def main(argv=None):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+
+    import synth
+    from paper_1001_3411_gb300 import Hop, build_library, default_params, radius_model
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=16777216)
+    ap.add_argument("--radius", choices=["plain", "count", "learned"], default="learned")
+    ap.add_argument("--qpw", type=int, default=4)
+    ap.add_argument("--cpr", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    a = ap.parse_args(argv)
+    build_library()
+    pos, _ = synth.nfw_box(a.n, synth.workload_seed(3))
+    d = torch.from_numpy(pos).cuda()
+    h = Hop(0)
+    h.set_tuning(a.qpw, a.cpr)
+    mode = {"plain": 0, "count": 1, "learned": 2}[a.radius]
+    if mode == 2:
+        w, m = radius_model.load()[a.qpw]
+        h.hop_mlp_load(w, m)
+    p = default_params(radius_mode=mode)
+    for i in range(a.steps):
+        r = h.hop_run(d, p)
+        print(json.dumps(dict(step=i, n_groups=r["n_groups"], **h.stats())), flush=True)
+    h.close()
+
+
+if __name__ == "__main__":
+    main()
