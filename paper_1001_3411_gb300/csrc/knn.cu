@@ -202,6 +202,63 @@ __device__ void warp_hist(bool need, const T *bd, int cnt, int cmax, int *hist, 
     }
 }
 
+// The same quantities as warp_hist, from the per-lane histogram rows kept
+// up to date while appending (bins relative to the window base tbw): the
+// group's P lanes each sum kHistBins/P bins over the P rows.  Returns false
+// in `ok` when the k-th (or n_out-th) entry lies in the open-ended lowest bin,
+// so the caller has to use warp_hist.
+template <int P>
+__device__ void rows_scan(bool need, const int *grows, int gtot, int k, int n_out, int p, uint32_t gmask,
+                          int &bk, int &bo, int &below_k, int &upto_k, bool &ok)
+{
+    constexpr int PER = kHistBins / P;
+    int mine = 0;
+    if (need) {
+#pragma unroll
+        for (int r = 0; r < P; ++r)
+#pragma unroll
+            for (int i = 0; i < PER; ++i) mine += grows[r * (kHistBins + 1) + p * PER + i];
+    }
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o, P);
+        if (p >= o) incl += y;
+    }
+    const int excl = incl - mine;
+    int fk = -1, fbelow = 0, fupto = 0, fo = -1;
+    if (need && excl < k && k <= incl) {
+        int cum = excl;
+        for (int i = 0; i < PER; ++i) {
+            int h = 0;
+#pragma unroll
+            for (int r = 0; r < P; ++r) h += grows[r * (kHistBins + 1) + p * PER + i];
+            if (cum + h >= k) { fk = p * PER + i; fbelow = cum; fupto = cum + h; break; }
+            cum += h;
+        }
+    }
+    if (need && n_out > 0 && excl < n_out && n_out <= incl) {
+        int cum = excl;
+        for (int i = 0; i < PER; ++i) {
+            int h = 0;
+#pragma unroll
+            for (int r = 0; r < P; ++r) h += grows[r * (kHistBins + 1) + p * PER + i];
+            if (cum + h >= n_out) { fo = p * PER + i; break; }
+            cum += h;
+        }
+    }
+    const uint32_t hk = __ballot_sync(FULL, fk >= 0) & gmask;
+    const uint32_t ho = __ballot_sync(FULL, fo >= 0) & gmask;
+    const int lk = hk ? __ffs(hk) - 1 : 0, lo = ho ? __ffs(ho) - 1 : 0;
+    const int gk = __shfl_sync(FULL, fk, lk), gbelow = __shfl_sync(FULL, fbelow, lk),
+              gupto = __shfl_sync(FULL, fupto, lk), go = __shfl_sync(FULL, fo, lo);
+    bk = hk ? gk : kHistBins - 1;
+    below_k = hk ? gbelow : 0;
+    upto_k = hk ? gupto : gtot;
+    bo = n_out <= 0 ? kHistBins - 1 : (ho ? go : kHistBins - 1);
+    ok = !need || (hk && bk > 0 && (n_out <= 0 || (ho && bo > 0)));
+}
+
 // Exact k-th smallest value of each needing group's buffer, given that it
 // lies in bin bk with below_k smaller entries: the entries of bin bk are
 // gathered into a small list and ranked there (the whole buffer is scanned
@@ -368,7 +425,8 @@ template <typename T, int P> struct WarpSmem {
     __host__ __device__ static size_t kth(int buf) { return rs(buf) + 68 * 4; }        // rs[32], ro[33], pad
     __host__ __device__ static size_t qpos(int buf) { return kth(buf) + sizeof(T) * Q; }
     __host__ __device__ static size_t cube(int buf) { return qpos(buf) + sizeof(T) * 3 * Q; }
-    __host__ __device__ static size_t kd(int buf) { return (cube(buf) + sizeof(int) * 6 * Q + 15) & ~size_t(15); }
+    __host__ __device__ static size_t hrow(int buf) { return (cube(buf) + sizeof(int) * 6 * Q + 15) & ~size_t(15); }
+    __host__ __device__ static size_t kd(int buf) { return hrow(buf) + sizeof(int) * 32 * (kHistBins + 1); }
     __host__ __device__ static size_t od(int buf) { return kd(buf) + sizeof(T) * Q * KCAP; }
     __host__ __device__ static size_t os(int buf) { return od(buf) + sizeof(T) * Q * OCAP; }
     __host__ __device__ static size_t total(int buf)
@@ -408,6 +466,9 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
     T *kthv = (T *)(wbase + L::kth(a.buf));
     T *qpos = (T *)(wbase + L::qpos(a.buf));      // Q x 3, real coordinates
     int *cube = (int *)(wbase + L::cube(a.buf));  // Q x 6: lo x3, n x3
+    int *hrows = (int *)(wbase + L::hrow(a.buf));             // one padded histogram row per lane
+    int *hr = hrows + lane * (kHistBins + 1);                   // this lane's row
+    int *grows = hrows + q * P * (kHistBins + 1);               // the group's rows
     T *kd = (T *)(wbase + L::kd(a.buf)) + q * KCAP;
     T *od = (T *)(wbase + L::od(a.buf)) + q * OCAP;
     uint32_t *os = (uint32_t *)(wbase + L::os(a.buf)) + q * OCAP;
@@ -439,6 +500,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
         if (!(R > T(0))) R = box * T(1e-6);
         T tau = R * R;
         int cnt = 0;
+        int tbw = 0;
         bool certified = false;
         int tries = 0;
 
@@ -465,6 +527,29 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
 
             tau = full ? T(INFINITY) : R * R;
             cnt = 0;
+            tbw = bin_base(tau);              // histogram window of this lane's row
+#pragma unroll
+            for (int b = 0; b < kHistBins; ++b) hr[b] = 0;
+            // candidates farther than R from every query are farther than
+            // R + (half-diagonal of the queries' box) from the box centre:
+            // staging drops them with one distance test
+            T fcx, fcy, fcz, rc2;
+            {
+                T lx = qx, ly = qy, lz = qz, hx = qx, hy = qy, hz = qz;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lx = min(lx, __shfl_xor_sync(FULL, lx, o));
+                    ly = min(ly, __shfl_xor_sync(FULL, ly, o));
+                    lz = min(lz, __shfl_xor_sync(FULL, lz, o));
+                    hx = max(hx, __shfl_xor_sync(FULL, hx, o));
+                    hy = max(hy, __shfl_xor_sync(FULL, hy, o));
+                    hz = max(hz, __shfl_xor_sync(FULL, hz, o));
+                }
+                fcx = T(0.5) * (lx + hx); fcy = T(0.5) * (ly + hy); fcz = T(0.5) * (lz + hz);
+                const T ex = T(0.5) * (hx - lx), ey = T(0.5) * (hy - ly), ez = T(0.5) * (hz - lz);
+                const T rc = R + sqrt(ex * ex + ey * ey + ez * ez);
+                rc2 = (full || pairwrap) ? T(INFINITY) : rc * rc * T(1.0001) + box * box * T(1e-12);
+            }
 
             int l = 1, G = 2;
             if (!full) {
@@ -581,21 +666,27 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                     };
                     if (total > 0) fetch(0);
                     for (uint32_t t0 = 0; t0 < total; t0 += TILE) {
-                        const int m = (int)min((uint32_t)TILE, total - t0);
+                        int m = 0;   // staged candidates that pass the chunk-sphere test
 #pragma unroll
                         for (int jj = 0; jj < PER_LANE; ++jj) {
-                            if (pidx[jj] == 0xffffffffu) continue;
-                            const typename V4<T>::type v = pv[jj];
                             Rec<T> rec;
-                            if (pairwrap) {
-                                rec.x = v.x; rec.y = v.y; rec.z = v.z;
-                            } else {
-                                rec.x = (wx && v.x >= half) ? v.x - box : v.x;
-                                rec.y = (wy && v.y >= half) ? v.y - box : v.y;
-                                rec.z = (wz && v.z >= half) ? v.z - box : v.z;
+                            bool keep = false;
+                            if (pidx[jj] != 0xffffffffu) {
+                                const typename V4<T>::type v = pv[jj];
+                                if (pairwrap) {
+                                    rec.x = v.x; rec.y = v.y; rec.z = v.z;
+                                } else {
+                                    rec.x = (wx && v.x >= half) ? v.x - box : v.x;
+                                    rec.y = (wy && v.y >= half) ? v.y - box : v.y;
+                                    rec.z = (wz && v.z >= half) ? v.z - box : v.z;
+                                }
+                                rec.s = pidx[jj];
+                                const T dx = rec.x - fcx, dy = rec.y - fcy, dz = rec.z - fcz;
+                                keep = dx * dx + dy * dy + dz * dz <= rc2;
                             }
-                            rec.s = pidx[jj];
-                            tile[lane + 32 * jj] = rec;
+                            const uint32_t kb = __ballot_sync(FULL, keep);
+                            if (keep) tile[m + __popc(kb & lt_mask)] = rec;
+                            m += __popc(kb);
                         }
                         __syncwarp();
                         if (t0 + TILE < total) fetch(t0 + TILE);
@@ -645,6 +736,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                                     bd[pos] = d2[u];
                                     bs[pos] = sj[u];
                                     ++pos;
+                                    ++hr[bin_of(d2[u], tbw)];
                                 }
                             }
                             cnt += gtot;
@@ -652,8 +744,13 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                             if (__any_sync(FULL, cnt > a.cap)) {
                                 const bool need = cnt > a.cap;
                                 const int cmax = warp_max_i(cnt);
-                                int tb, bk, bo, below_k, upto_k;
-                                warp_hist<T, P>(need, bd, cnt, cmax, hist, k, 0, p, gmask, tb, bk, bo, below_k, upto_k);
+                                int tb = tbw, bk, bo, below_k, upto_k;
+                                bool rows_ok;
+                                __syncwarp();
+                                rows_scan<P>(need, grows, cnt, k, 0, p, gmask, bk, bo, below_k, upto_k, rows_ok);
+                                if (!__all_sync(FULL, rows_ok))
+                                    warp_hist<T, P>(need, bd, cnt, cmax, hist, k, 0, p, gmask, tb, bk, bo, below_k,
+                                                    upto_k);
                                 // the bin edge shrinks the buffer only if the k-th entry's bin
                                 // is not crowded (candidates in a distant dense clump can share
                                 // one bin); otherwise cut at the exact k-th value
@@ -673,6 +770,16 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                                         if (p == 0) atomicOr(a.err, kErrDegenerate);
                                         cnt = a.cap;
                                     }
+                                    // rebuild this group's rows for the new window
+                                    tbw = bin_base(tau);
+#pragma unroll
+                                    for (int b = 0; b < kHistBins; ++b) hr[b] = 0;
+                                }
+                                __syncwarp();
+                                const int cmax2 = warp_max_i(need ? cnt : 0);
+                                for (int e0 = 0; e0 < cmax2; e0 += P) {
+                                    const int e = e0 + p;
+                                    if (need && e < cnt) ++hr[bin_of(bd[e], tbw)];
                                 }
                             }
                         }
@@ -707,9 +814,74 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
             const bool need = active;
             const int n_out = (a.nbr_s != nullptr) ? a.n_out : 0;
             const int cmax = warp_max_i(cnt);
-            int tb, bk, bo, below_k, upto_k;
-            warp_hist<T, P>(need, bd, cnt, cmax, hist, k, n_out, p, gmask, tb, bk, bo, below_k, upto_k);
-            warp_kth<T, P>(need, bd, cnt, cmax, tb, bk, below_k, k, p, gmask, lt_mask, kd, &kthv[q]);
+            int tb = tbw, bk, bo, below_k, upto_k;
+            bool rows_ok;
+            __syncwarp();
+            rows_scan<P>(need, grows, cnt, k, n_out, p, gmask, bk, bo, below_k, upto_k, rows_ok);
+            if (!__all_sync(FULL, rows_ok))
+                warp_hist<T, P>(need, bd, cnt, cmax, hist, k, n_out, p, gmask, tb, bk, bo, below_k, upto_k);
+            // one pass gathers the k-th entry's bin (for the exact r_k) and
+            // the entries up to the n_out-th entry's bin (for the list)
+            int nk = 0, no = 0;
+            for (int e0 = 0; e0 < cmax; e0 += P) {
+                const int e = e0 + p;
+                T v = T(0);
+                bool ink = false, ino = false;
+                if (need && e < cnt) {
+                    v = bd[e];
+                    const int b = bin_of(v, tb);
+                    ink = b == bk;
+                    ino = n_out > 0 && b <= bo;
+                }
+                const uint32_t mk = __ballot_sync(FULL, ink) & gmask;
+                const uint32_t mo = __ballot_sync(FULL, ino) & gmask;
+                if (ink) {
+                    const int pos = nk + __popc(mk & lt_mask);
+                    if (pos < KCAP) kd[pos] = v;
+                }
+                if (ino) {
+                    const int pos = no + __popc(mo & lt_mask);
+                    if (pos < OCAP) { od[pos] = v; os[pos] = bs[e]; }
+                }
+                nk += __popc(mk);
+                no += __popc(mo);
+            }
+            __syncwarp();
+            {
+                const bool small = nk <= KCAP;
+                const int nkmax = warp_max_i((need && small) ? nk : 0);
+                for (int e0 = 0; e0 < nkmax; e0 += P) {
+                    const int e = e0 + p;
+                    const bool mine = need && small && e < nk;
+                    const T v = mine ? kd[e] : T(0);
+                    int lt = below_k, le = below_k;
+                    for (int f = 0; f < nkmax; ++f) {
+                        if (f < nk) {
+                            const T u = kd[f];
+                            lt += u < v;
+                            le += u <= v;
+                        }
+                    }
+                    if (mine && lt < k && k <= le) kthv[q] = v;
+                }
+                if (__any_sync(FULL, need && !small)) {
+                    for (int e0 = 0; e0 < cmax; e0 += P) {
+                        const int e = e0 + p;
+                        if (!(need && !small && e < cnt)) continue;
+                        const T v = bd[e];
+                        if (bin_of(v, tb) != bk) continue;
+                        int lt = below_k, le = below_k;
+                        for (int f = 0; f < cnt; ++f) {
+                            const T u = bd[f];
+                            if (bin_of(u, tb) != bk) continue;
+                            lt += u < v;
+                            le += u <= v;
+                        }
+                        if (lt < k && k <= le) kthv[q] = v;
+                    }
+                }
+                __syncwarp();
+            }
             const T vk = kthv[q];
             // density: fixed-point sum of w(2 r / r_k) over entries with d^2 < r_k^2
             unsigned long long wsum = 0;
@@ -727,26 +899,9 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
             }
 #pragma unroll
             for (int o = 1; o < P; o <<= 1) wsum += __shfl_xor_sync(FULL, wsum, o);
-            // the n_out nearest in (d^2, original index) order, ranked in a
-            // small list of the entries up to the n_out-th entry's bin
+            // the n_out nearest in (d^2, original index) order, ranked in the
+            // small list (the whole buffer only when that list overflowed)
             if (n_out > 0) {
-                int no = 0;
-                for (int e0 = 0; e0 < cmax; e0 += P) {
-                    const int e = e0 + p;
-                    T v = T(0);
-                    bool in = false;
-                    if (need && e < cnt) {
-                        v = bd[e];
-                        in = bin_of(v, tb) <= bo;
-                    }
-                    const uint32_t m = __ballot_sync(FULL, in) & gmask;
-                    if (in) {
-                        const int pos = no + __popc(m & lt_mask);
-                        if (pos < OCAP) { od[pos] = v; os[pos] = bs[e]; }
-                    }
-                    no += __popc(m);
-                }
-                __syncwarp();
                 const bool small = no <= OCAP;
                 const int nomax = warp_max_i((need && small) ? no : 0);
                 for (int e0 = 0; e0 < nomax; e0 += P) {
@@ -829,7 +984,9 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     d.k = a.k;
     d.n_out = a.n_out;
     d.ld_out = a.ld_out;
-    d.cap = 4 * a.k;   // room for 4 Ndens entries per query: compactions are rare
+    // room for 4 Ndens entries per query (3 with 8 or more queries per warp,
+    // where the larger buffer would cost a resident block): compactions are rare
+    d.cap = (Q <= 4 ? 4 : 3) * a.k;
     d.buf = d.cap + 4 * P + 4;
     d.chunk_r = a.chunk_r;
     d.plain_r = a.plain_r;
