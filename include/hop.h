@@ -176,6 +176,61 @@ int hop_run(hop_ctx *ctx, const void *pos, int64_t n, const hop_params *params,
             uint32_t *nbr, int32_t ld_nbr, uint32_t *chain);
 
 /*
+ * Many independent periodic subvolumes in one pass (Parallel HOP Sec. 3
+ * runs subvolumes as separate tasks; here they are independent problems
+ * run together).  Subvolume b holds particles [offsets[b], offsets[b+1])
+ * of pos, in its own periodic box [0, boxes[b])^3.  Each subvolume's
+ * result is exactly that of hop_run on it alone: the same densities, the
+ * same neighbour lists (offset by offsets[b]), the same group ids.
+ *   pos      N x 3 float32 (N = offsets[B]), device or host memory.
+ *   offsets  B + 1 int64 (host), offsets[0] = 0, every subvolume holding at
+ *            least n_dens particles; N < 2^31 - 1.
+ *   boxes    B float64 (host), each > 0.  params->box is not used and
+ *            params->pos_is_f64 must be 0.
+ *   dens     N float32, device or host, or NULL.
+ *   group    N int32, device or host: -1, or the rank of the particle's
+ *            group within its own subvolume (ordered as in hop_merge).
+ *   n_groups B int64 (host): groups per subvolume.
+ *   nbr      N x ld_nbr uint32 device (indices into the whole batch), or NULL.
+ *   flags    0: the pass is captured into a CUDA graph (kept by the context
+ *            and replayed while the subvolumes, parameters, tuning and
+ *            buffers stay the same); HOP_BATCH_EAGER: kernels are enqueued
+ *            one by one and the merge loops are driven from the host.
+ * Queries per warp must be 4, 8 or 16 (hop_set_tuning); with
+ * HOP_RADIUS_LEARNED the network loaded for that setting is used.  Stage
+ * times in hop_stats are those of the pass on the device.  Synchronises the
+ * stream.
+ */
+#define HOP_BATCH_EAGER 1
+int hop_run_batch(hop_ctx *ctx, const float *pos, const int64_t *offsets, const double *boxes,
+                  int32_t B, const hop_params *params, float *dens, int32_t *group,
+                  int64_t *n_groups, uint32_t *nbr, int32_t ld_nbr, int32_t flags);
+
+/* Tuning of the kNN search: queries per warp (the lanes of a warp split
+ * into 32 / qpw lanes per query), search cells per radius (the cell side is
+ * about radius / cpr), and the per-query candidate buffer in units of
+ * n_dens (buf_factor 2, 3 or 4; 0 = 4 up to 4 queries per warp, else 3).
+ * ms is the autotuner's measured pass time (-1 if the candidate was
+ * skipped). */
+typedef struct hop_tuning {
+    int32_t qpw, cpr, buf_factor;
+    float ms;
+} hop_tuning;
+int hop_get_tuning(const hop_ctx *ctx, hop_tuning *out);
+int hop_apply_tuning(hop_ctx *ctx, const hop_tuning *t);
+
+/*
+ * Times the batched pass (graph replays, median of reps) for each of n_cand
+ * candidates on the given batch, writes each candidate's ms, and applies
+ * the fastest; *best = its index.  Candidates with a qpw other than 4, 8,
+ * 16, or (learned radius) with no network loaded for their qpw, are
+ * skipped.  Results do not depend on the tuning.  Synchronises the stream.
+ */
+int hop_autotune(hop_ctx *ctx, const float *pos, const int64_t *offsets, const double *boxes,
+                 int32_t B, const hop_params *params, hop_tuning *cand, int32_t n_cand,
+                 int32_t reps, int32_t *best);
+
+/*
  * hop_link without any device allocation.  (No counterpart in the paper:
  * this is an interface for callers, not part of the method.)
  *
@@ -232,7 +287,10 @@ int hop_get_stats(const hop_ctx *ctx, hop_stats *out);
 #define HOP_MLP_NPARAM (64 * 27 + 64 + 64 * 64 + 64 + 64 + 1)
 
 /* Loads fp32 parameters (host) and the radius margin added to the predicted
- * log radius before the search. */
+ * log radius before the search.  A context keeps one network per
+ * queries-per-warp setting (the chunk features depend on it): this call,
+ * and the other hop_mlp_* calls, act on the network of the current
+ * setting (hop_set_tuning). */
 int hop_mlp_load(hop_ctx *ctx, const float *params_host, float log_margin);
 /* Copies the current fp32 master parameters to the host. */
 int hop_mlp_get(hop_ctx *ctx, float *params_host);

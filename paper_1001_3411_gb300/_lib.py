@@ -19,6 +19,7 @@ HOP_OK, HOP_EINVAL, HOP_ENOMEM, HOP_ECUDA, HOP_ETABLE, HOP_ETIMEOUT, HOP_EDEGENE
 HOP_ESTATIC = 8
 HOP_STATIC_LINK_MAX_N = 1 << 20
 HOP_RADIUS_PLAIN, HOP_RADIUS_COUNT, HOP_RADIUS_LEARNED = 0, 1, 2
+HOP_BATCH_EAGER = 1
 MLP_IN, MLP_HID = 27, 64
 MLP_NPARAM = 64 * 27 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -28,7 +29,8 @@ ERROR_NAMES = {0: "HOP_OK", 1: "HOP_EINVAL", 2: "HOP_ENOMEM", 3: "HOP_ECUDA", 4:
 EXPORTS = ["hop_default_params", "hop_create", "hop_destroy", "hop_set_stream", "hop_last_error",
            "hop_set_tuning", "hop_density", "hop_link", "hop_boundaries", "hop_merge", "hop_run",
            "hop_get_stats", "hop_mlp_load", "hop_mlp_get", "hop_mlp_samples", "hop_mlp_forward",
-           "hop_mlp_grad", "hop_mlp_train", "hop_link_static"]
+           "hop_mlp_grad", "hop_mlp_train", "hop_link_static", "hop_run_batch", "hop_get_tuning",
+           "hop_apply_tuning", "hop_autotune"]
 
 
 class HopParams(C.Structure):
@@ -45,6 +47,13 @@ class HopStats(C.Structure):
                 ("n_edges", C.c_int64), ("n_groups", C.c_int64),
                 ("knn_queries_per_warp", C.c_int32), ("knn_cells_per_radius", C.c_int32),
                 ("launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HopTuning(C.Structure):
+    _fields_ = [("qpw", C.c_int32), ("cpr", C.c_int32), ("buf_factor", C.c_int32), ("ms", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +101,11 @@ def load_library(path: str = LIB):
             "hop_mlp_grad": (C.c_int, [vp, vp, vp, i64, C.POINTER(f64), vp]),
             "hop_mlp_train": (C.c_int, [vp, vp, vp, i64, i32, i32, f32, C.c_uint64, C.POINTER(f64)]),
             "hop_link_static": (C.c_int, [vp, vp, i32, i64, i32, vp, vp, vp]),
+            "hop_run_batch": (C.c_int, [vp, vp, vp, vp, i32, P, vp, vp, vp, vp, i32, i32]),
+            "hop_get_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
+            "hop_apply_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
+            "hop_autotune": (C.c_int, [vp, vp, vp, vp, i32, P, C.POINTER(HopTuning), i32, i32,
+                                       C.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -252,6 +266,64 @@ class Hop:
         self._check(self.L.hop_run(self.h, _ptr(pos), n, C.byref(params), _ptr(dens), _ptr(group),
                                    C.byref(ng), _ptr(nbr), ld_nbr or 0, _ptr(chain)))
         return dict(dens=dens, group=group, n_groups=ng.value, nbr=nbr, chain=chain)
+
+    def hop_run_batch(self, pos, offsets, boxes, params: HopParams, ld_nbr: int | None = None,
+                      want_dens=True, eager=False, out=None):
+        """Many periodic subvolumes in one pass.  ``pos`` (N x 3 float32) is a
+        CUDA tensor or a host array; ``offsets`` (B + 1) and ``boxes`` (B)
+        are host sequences.  Group ids are ranks within each subvolume;
+        ``n_groups`` is a numpy array of B counts."""
+        import torch
+        self._sync_stream()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64))
+        B = len(bx)
+        if off.shape != (B + 1,):
+            raise ValueError("offsets must hold B + 1 entries")
+        host = isinstance(pos, np.ndarray) or (isinstance(pos, torch.Tensor) and not pos.is_cuda)
+        if isinstance(pos, np.ndarray) and pos.dtype != np.float32:
+            raise TypeError("pos must be float32")
+        n = pos.shape[0]
+        if tuple(pos.shape) != (int(off[-1]), 3):
+            raise ValueError(f"pos must have shape ({int(off[-1])}, 3), got {tuple(pos.shape)}")
+        if out is not None:
+            dens, group = out.get("dens"), out["group"]
+        elif host:
+            pin = isinstance(pos, torch.Tensor) and pos.is_pinned()
+            group = torch.empty(n, dtype=torch.int32, pin_memory=pin)
+            dens = torch.empty(n, dtype=torch.float32, pin_memory=pin) if want_dens else None
+        else:
+            _need(pos, torch.float32, (n, 3), "pos")
+            group = torch.empty(n, dtype=torch.int32, device=pos.device)
+            dens = torch.empty(n, dtype=torch.float32, device=pos.device) if want_dens else None
+        dev = torch.device("cuda", self.device)
+        nbr = torch.empty((n, ld_nbr), dtype=torch.int32, device=dev) if ld_nbr else None
+        ng = np.zeros(B, dtype=np.int64)
+        self._check(self.L.hop_run_batch(self.h, _ptr(pos), _ptr(off), _ptr(bx), B, C.byref(params),
+                                         _ptr(dens), _ptr(group), _ptr(ng), _ptr(nbr), ld_nbr or 0,
+                                         HOP_BATCH_EAGER if eager else 0))
+        return dict(dens=dens, group=group, n_groups=ng, nbr=nbr)
+
+    def get_tuning(self) -> dict:
+        t = HopTuning()
+        self._check(self.L.hop_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def apply_tuning(self, qpw: int, cpr: int, buf_factor: int = 0):
+        t = HopTuning(qpw, cpr, buf_factor, 0.0)
+        self._check(self.L.hop_apply_tuning(self.h, C.byref(t)))
+
+    def hop_autotune(self, pos, offsets, boxes, params: HopParams, candidates, reps: int = 3):
+        """Times each (qpw, cpr, buf_factor) candidate on the batched pass and
+        applies the fastest; returns (best index, [dict per candidate])."""
+        self._sync_stream()
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64))
+        arr = (HopTuning * len(candidates))(*[HopTuning(q, c, f, 0.0) for q, c, f in candidates])
+        best = C.c_int32(-1)
+        self._check(self.L.hop_autotune(self.h, _ptr(pos), _ptr(off), _ptr(bx), len(bx), C.byref(params),
+                                        arr, len(candidates), reps, C.byref(best)))
+        return best.value, [a.as_dict() for a in arr]
 
     def stats(self) -> dict:
         st = HopStats()

@@ -25,12 +25,18 @@ void *ctx_buf(hop_ctx *c, Slot s, size_t bytes)
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return b.p;
     if (b.p) {
-        // work already enqueued may still use the old buffer
-        cudaStreamSynchronize(c->stream);
-        cudaFree(b.p);
+        if (c->capturing) {
+            // nodes captured earlier use the old buffer: keep it with the graph
+            c->graveyard.push_back(b.p);
+        } else {
+            // work already enqueued may still use the old buffer
+            cudaStreamSynchronize(c->stream);
+            cudaFree(b.p);
+        }
         b.p = nullptr;
         b.cap = 0;
     }
+    ++c->buf_epoch;   // a cached graph that used this slot is stale
     size_t want = bytes + bytes / 8;
     want = (want + (size_t(2) << 20) - 1) & ~((size_t(2) << 20) - 1);
     cudaError_t e = cudaMalloc(&b.p, want);
@@ -63,6 +69,7 @@ int ctx_check_device_error(hop_ctx *c)
         return ctx_fail(c, HOP_EDEGENERATE, "more equidistant neighbours than the search buffer holds");
     if (e & kErrKnnRetry) return ctx_fail(c, HOP_ETIMEOUT, "kNN search did not certify");
     if (e & kErrChainLoop) return ctx_fail(c, HOP_ETIMEOUT, "chain following did not end");
+    if (e & kErrMergeLoop) return ctx_fail(c, HOP_ETIMEOUT, "merge rounds did not converge");
     if (e & kErrTableFull) return ctx_fail(c, HOP_ENOMEM, "boundary table full");
     return ctx_fail(c, HOP_ECUDA, "device error word " + std::to_string(e));
 }
@@ -94,14 +101,6 @@ int check_params(hop_ctx *c, const hop_params *p, int64_t n)
     return HOP_OK;
 }
 
-// First search radius of the plain path: the side of the base-grid cell
-// holding about 64 particles at the box's mean density, times 2^level.
-float plain_radius(int64_t n, double box)
-{
-    int lb = 0;
-    while (lb < 15 && (int64_t(1) << (3 * (lb + 1))) * 16 <= n) ++lb;
-    return (float)(box / (double)(1 << lb));
-}
 
 void ev_record(hop_ctx *c, int i) { cudaEventRecord(c->ev[i], c->stream); }
 
@@ -145,7 +144,7 @@ int density_core(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, in
         rc = chunk_radius(c, st->spos, st->keys, st->cellT, st->Ld, n, p, qpw, chunk_r);
         if (rc) return rc;
     } else if (p->radius_mode == HOP_RADIUS_LEARNED) {
-        if (!c->mlp.loaded) return ctx_fail(c, HOP_ENOMODEL, "no radius network loaded (hop_mlp_load)");
+        if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no radius network loaded (hop_mlp_load)");
         chunk_r = (float *)ctx_buf(c, S_CHUNK_R, n_chunks * sizeof(float));
         if (!chunk_r) return HOP_ENOMEM;
         rc = mlp_radius(c, st->spos, st->keys, st->cellT, st->Ld, n, p, qpw, chunk_r);
@@ -168,7 +167,7 @@ int density_core(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, in
     a.n_out = n_out;
     a.ld_out = st->ld_s;
     a.chunk_r = chunk_r;
-    a.plain_r = plain_radius(n, p->box);
+    a.plain_r = plain_radius_for(n, p->box);
     a.nbr_s = st->nbr_s;
     a.dens_s = st->dens_s;
     a.rk_s = st->rk_s;
@@ -250,6 +249,9 @@ void hop_destroy(hop_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    batch_free(c);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (int i = 0; i < S_COUNT; ++i)
         if (c->buf[i].p) cudaFree(c->buf[i].p);
     if (c->d_err) cudaFree(c->d_err);
@@ -276,7 +278,10 @@ int hop_set_tuning(hop_ctx *c, int32_t qpw, int32_t cpr)
     if (qpw != 0 && qpw != 1 && qpw != 2 && qpw != 4 && qpw != 8 && qpw != 16 && qpw != 32)
         return ctx_fail(c, HOP_EINVAL, "queries per warp must be 1, 2, 4, 8, 16 or 32");
     if (cpr < 0 || cpr > 4) return ctx_fail(c, HOP_EINVAL, "cells per radius must be 1 to 4");
-    if (qpw) c->qpw = qpw;
+    if (qpw) {
+        c->qpw = qpw;
+        c->mlp = c->mlp_bank + qpw_index(qpw);
+    }
     if (cpr) c->cpr = cpr;
     return HOP_OK;
 }

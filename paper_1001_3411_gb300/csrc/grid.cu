@@ -42,14 +42,44 @@ __global__ void keys_kernel(const T *__restrict__ pos, int64_t n, T box, T inv_b
     }
 }
 
+// Batched pass: the key leads with the subvolume number (bits 48..63), so
+// one sort orders particles by subvolume, then by Morton key in its own box.
+template <typename T>
+__global__ void keys_seg_kernel(const T *__restrict__ pos, int64_t n, const SegDesc *__restrict__ seg,
+                                int B, uint64_t *__restrict__ keys, uint32_t *__restrict__ idx,
+                                uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = seg_of_index(seg, B, i);
+        const double bd = seg[b].box;
+        const T box = (T)bd, inv_box = (T)(1.0 / bd);
+        T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        const bool ok = x >= T(0) && x < box && y >= T(0) && y < box && z >= T(0) && z < box;
+        if (!ok) {
+            atomicOr(err, kErrBadPos);
+            x = y = z = T(0);
+        }
+        const uint32_t qx = min((uint32_t)(x * inv_box * T(65536)), 65535u);
+        const uint32_t qy = min((uint32_t)(y * inv_box * T(65536)), 65535u);
+        const uint32_t qz = min((uint32_t)(z * inv_box * T(65536)), 65535u);
+        keys[i] = ((uint64_t)b << 48) | morton3(qx, qy, qz);
+        idx[i] = (uint32_t)i;
+    }
+}
+
+// Sorted float4 records; with kout set, also the sorted keys without the
+// subvolume field (the Morton key within the particle's own box).
 template <typename T>
 __global__ void gather_kernel(const T *__restrict__ pos, const uint32_t *__restrict__ perm,
-                              int64_t n, typename V4<T>::type *__restrict__ spos)
+                              int64_t n, typename V4<T>::type *__restrict__ spos,
+                              const uint64_t *__restrict__ kin, uint64_t *__restrict__ kout)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = perm[s];
         spos[s] = make_rec(pos[3 * (int64_t)p], pos[3 * (int64_t)p + 1], pos[3 * (int64_t)p + 2], p);
+        if (kout) kout[s] = kin[s] & ((uint64_t(1) << 48) - 1);
     }
 }
 
@@ -63,6 +93,28 @@ __global__ void cell_table_kernel(const uint64_t *__restrict__ keys, int64_t n, 
         const int64_t cs = s < n ? (int64_t)(keys[s] >> shift) : ncell;
         const int64_t cp = s > 0 ? (int64_t)(keys[s - 1] >> shift) : -1;
         for (int64_t c = cp + 1; c <= cs; ++c) cellT[c] = (uint32_t)s;
+    }
+}
+
+// Batched pass: every subvolume's table at its own dense level, entries
+// holding global sorted positions, from the keys that still carry the
+// subvolume field.
+__global__ void cell_table_seg_kernel(const uint64_t *__restrict__ keys, int64_t n,
+                                      const SegDesc *__restrict__ seg, uint32_t *__restrict__ cellT)
+{
+    const uint64_t m48 = (uint64_t(1) << 48) - 1;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[s];
+        const SegDesc &d = seg[key >> 48];
+        const int shift = 3 * (kMaxLevel - d.level_dense);
+        const int64_t ncell = int64_t(1) << (3 * d.level_dense);
+        uint32_t *t = cellT + d.cell0;
+        const int64_t cs = (int64_t)((key & m48) >> shift);
+        const int64_t cp = s > d.base ? (int64_t)((keys[s - 1] & m48) >> shift) : -1;
+        for (int64_t c = cp + 1; c <= cs; ++c) t[c] = (uint32_t)s;
+        if (s == d.base + d.n - 1)
+            for (int64_t c = cs + 1; c <= ncell; ++c) t[c] = (uint32_t)(s + 1);
     }
 }
 
@@ -100,21 +152,37 @@ __device__ __forceinline__ void cell_range_g(const uint32_t *__restrict__ cellT,
 //   feat[c][27] = log(1 + count), lvl[c], the closed-form radius
 //   R = side * (81 k / (4 pi sum counts))^(1/3) * exp(log_margin)
 //   (the radius of a ball holding k particles at the stencil's mean
-//   density), and the training target log(max r_k over the chunk / side).
+//   density), the cell side itself, and the training target
+//   log(max r_k over the chunk / side).
+// With seg set (a batched pass) each chunk uses its subvolume's box, cell
+// table and particle range.
 template <typename T>
 __global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
                                   const uint64_t *__restrict__ keys,
-                                  const uint32_t *__restrict__ cellT, int Ld, int64_t n,
-                                  int64_t n_chunks, int Q, T box, T inv_box, int k,
+                                  const uint32_t *__restrict__ cellT_all, int Ld_all, int64_t n_all,
+                                  int64_t n_chunks, int Q, T box_all, T inv_box_all, int k,
                                   float log_margin, float *__restrict__ chunk_r,
                                   float *__restrict__ feat, uint8_t *__restrict__ lvl,
-                                  const float *__restrict__ rk_s, float *__restrict__ target)
+                                  const float *__restrict__ rk_s, float *__restrict__ target,
+                                  const SegDesc *__restrict__ seg, int B, float *__restrict__ side_out)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t ch = warp0; ch < n_chunks; ch += nwarps) {
-        const int64_t s0 = ch * Q;
+        int64_t s0 = ch * Q, n = n_all;
+        const uint32_t *cellT = cellT_all;
+        int Ld = Ld_all;
+        T box = box_all, inv_box = inv_box_all;
+        if (seg) {
+            const SegDesc &d = seg[seg_of_chunk(seg, B, ch)];
+            s0 = d.base + (ch - d.chunk0) * Q;
+            n = d.base + d.n;
+            cellT = cellT_all + d.cell0;
+            Ld = d.level_dense;
+            box = (T)d.box;
+            inv_box = (T)(1.0 / d.box);
+        }
         const int nq = (int)min((int64_t)Q, n - s0);
         const int64_t s = s0 + (lane < nq ? lane : 0);
         const typename V4<T>::type v = spos[s];
@@ -153,6 +221,7 @@ __global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
         if (lane == 0) {
             const double side = (double)box / (double)G;
             if (lvl) lvl[ch] = (uint8_t)l;
+            if (side_out) side_out[ch] = (float)side;
             if (chunk_r) {
                 const double r = side * cbrt(81.0 * k / (4.0 * 3.14159265358979323846 * (double)max(tot, 1u)));
                 chunk_r[ch] = (float)(r * exp((double)log_margin));
@@ -182,7 +251,7 @@ int grid_build_t(hop_ctx *c, const T *pos, int64_t n, double box, void **spos_ou
     HOP_LAUNCH(c);
     int rc = radix_sort_u64(c, k0, k1, v0, v1, n, 0, 48, tmp);
     if (rc) return rc;
-    gather_kernel<T><<<blocks, 256, 0, c->stream>>>(pos, v0, n, spos);
+    gather_kernel<T><<<blocks, 256, 0, c->stream>>>(pos, v0, n, spos, nullptr, nullptr);
     HOP_LAUNCH(c);
     int blocks2 = (int)std::min<int64_t>((n + 256) / 256, (int64_t)c->num_sms * 32);
     cell_table_kernel<<<blocks2, 256, 0, c->stream>>>(k0, n, 3 * (kMaxLevel - Ld), ncell, cellT);
@@ -206,7 +275,7 @@ int chunk_feat_launch(hop_ctx *c, const void *spos, const uint64_t *keys, const 
     if (blocks < 1) blocks = 1;
     chunk_feat_kernel<T><<<(unsigned)blocks, 256, 0, c->stream>>>(
         (const typename V4<T>::type *)spos, keys, cellT, Ld, n, n_chunks, qpw, (T)box,
-        (T)(1.0 / box), k, log_margin, chunk_r, feat, lvl, rk_s, target);
+        (T)(1.0 / box), k, log_margin, chunk_r, feat, lvl, rk_s, target, nullptr, 0, nullptr);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -245,4 +314,55 @@ int chunk_features(hop_ctx *c, const void *spos, const uint64_t *keys, const uin
                                          feat, lvl, rk_s, target);
     return chunk_feat_launch<float>(c, spos, keys, cellT, Ld, n, box, qpw, 64, 0.f, nullptr, feat,
                                     lvl, rk_s, target);
+}
+
+// ------------------------------------------------------- batched pass ----
+int grid_build_seg(hop_ctx *c, const float *pos, int64_t n, const SegDesc *seg, int B,
+                   int64_t n_cells, void **spos_out, uint32_t **perm_out, uint64_t **keys_out,
+                   uint32_t **cellT_out)
+{
+    uint64_t *k0 = (uint64_t *)ctx_buf(c, S_KEY0, n * sizeof(uint64_t));
+    uint64_t *k1 = (uint64_t *)ctx_buf(c, S_KEY1, n * sizeof(uint64_t));
+    uint32_t *v0 = (uint32_t *)ctx_buf(c, S_VAL0, n * sizeof(uint32_t));
+    uint32_t *v1 = (uint32_t *)ctx_buf(c, S_VAL1, n * sizeof(uint32_t));
+    void *tmp = ctx_buf(c, S_SORT_TMP, radix_sort_scratch_bytes(n));
+    float4 *spos = (float4 *)ctx_buf(c, S_SPOS, n * sizeof(float4));
+    uint32_t *cellT = (uint32_t *)ctx_buf(c, S_CELLT, n_cells * sizeof(uint32_t));
+    if (!k0 || !k1 || !v0 || !v1 || !tmp || !spos || !cellT) return HOP_ENOMEM;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 32);
+    if (blocks < 1) blocks = 1;
+    keys_seg_kernel<float><<<blocks, 256, 0, c->stream>>>(pos, n, seg, B, k0, v0, c->d_err);
+    HOP_LAUNCH(c);
+    int sub_bits = 0;
+    while ((1 << sub_bits) < B) sub_bits += 8;
+    int rc = radix_sort_u64(c, k0, k1, v0, v1, n, 0, 48 + sub_bits, tmp);
+    if (rc) return rc;
+    // k0: sorted keys with the subvolume field; k1: the same without it
+    gather_kernel<float><<<blocks, 256, 0, c->stream>>>(pos, v0, n, spos, k0, k1);
+    HOP_LAUNCH(c);
+    cell_table_seg_kernel<<<blocks, 256, 0, c->stream>>>(k0, n, seg, cellT);
+    HOP_LAUNCH(c);
+    *spos_out = spos;
+    *perm_out = v0;
+    *keys_out = k1;
+    *cellT_out = cellT;
+    return HOP_OK;
+}
+
+// Per-chunk features of a batched pass.  With feat == nullptr the closed-form
+// radius goes to chunk_r; otherwise feat, lvl and the cell side (in chunk_r,
+// which the network's radius pass scales in place) are written.
+int chunk_feat_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r,
+                   float *feat, uint8_t *lvl)
+{
+    int64_t blocks = (n_chunks + 7) / 8;
+    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 16);
+    if (blocks < 1) blocks = 1;
+    const bool closed = feat == nullptr;
+    chunk_feat_kernel<float><<<(unsigned)blocks, 256, 0, c->stream>>>(
+        (const float4 *)spos, keys, cellT, 0, 0, n_chunks, qpw, 1.f, 1.f, k, 0.25f,
+        closed ? chunk_r : nullptr, feat, lvl, nullptr, nullptr, seg, B, closed ? nullptr : chunk_r);
+    HOP_LAUNCH(c);
+    return HOP_OK;
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "hop.h"
 
@@ -52,6 +53,8 @@ enum Slot {
     S_OUT_DENS, S_OUT_GROUP,            // device staging of host outputs
     S_GROUP_OUT,                        // group ids in sorted order
     S_ESORT_K0, S_ESORT_K1, S_ESORT_V0, S_ESORT_V1, S_ESORT_TMP,   // edge-list sort
+    S_SEG,                              // subvolume descriptors of a batched pass
+    S_BATCH,                            // per-pass arrays of a batched pass
     S_COUNT
 };
 
@@ -80,9 +83,18 @@ struct hop_ctx {
     void *h_pinned = nullptr;           // small pinned host staging area
     hop_stats stats{};
     int64_t launches = 0;               // kernels launched (all calls)
-    MlpState mlp;
+    MlpState mlp_bank[6];               // one network per queries-per-warp setting
+    MlpState *mlp = mlp_bank + 3;       // the network of the current setting
     int qpw = 8;                        // kNN queries per warp
     int cpr = 1;                        // search cells per radius
+    int capf = 0;                       // search buffer per query in Ndens (0: 4, or 3 from 8 queries per warp)
+    // graph capture of the batched pass
+    bool capturing = false;             // a capture is open on `stream`
+    std::vector<void *> graveyard;      // buffers replaced while capturing, freed with the graph
+    uint64_t buf_epoch = 0;             // bumped whenever a slot's buffer moves
+    struct BatchGraph *batch = nullptr; // cached graph of the last batched pass
+    cudaStream_t side = nullptr;        // capture stream of loop bodies
+    cudaStream_t cap = nullptr;         // capture stream of a pass (the caller's may be the legacy stream)
     // sorted state of the last density pass (for hop_mlp_samples)
     int64_t last_n = 0;
     int last_level_dense = 0;
@@ -96,6 +108,13 @@ struct hop_ctx {
     const float *last_rk = nullptr;
     cudaEvent_t ev[12] = {};
 };
+
+inline int qpw_index(int qpw)
+{
+    int i = 0;
+    while (i < 5 && (1 << i) < qpw) ++i;
+    return i;
+}
 
 // Counters slot indices in d_counters.
 enum { kCntCand = 0, kCntSearch, kCntRetry, kCntWarps, kCntQual, kCntEdges, kCntNum };
@@ -145,11 +164,75 @@ inline int dense_level_for(int64_t n)
     return l < 10 ? l + 1 : 10;
 }
 
+// First search radius of the plain path: the side of the coarsest grid
+// cell holding fewer than 1024 particles at the box's mean density (the
+// level l with 128 <= n / 8^l < 1024).
+inline float plain_radius_for(int64_t n, double box)
+{
+    int lb = 0;
+    while (lb < 15 && (int64_t(1) << (3 * (lb + 1))) * 16 <= n) ++lb;
+    return (float)(box / (double)(1 << lb));
+}
+
+// ------------------------------------------------------------ batches ----
+// One subvolume of a batched pass.  Its particles are the contiguous range
+// [base, base + n) both in the caller's order and after the sort (the sort
+// key leads with the subvolume number); its query chunks are
+// [chunk0, chunk0 + ceil(n / Q)); its dense cell table (level level_dense,
+// entries holding global sorted positions) starts at cell0.
+struct SegDesc {
+    int64_t base, n, chunk0, cell0;
+    double box;
+    double norm;          // box^3 / (n pi): density normalisation
+    float plain_r;
+    int level_dense;
+};
+
+// The subvolume holding chunk `ch`: the last b with seg[b].chunk0 <= ch.
+__device__ __forceinline__ int seg_of_chunk(const SegDesc *__restrict__ seg, int B, int64_t ch)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (seg[m].chunk0 <= ch) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
+
+// The subvolume holding particle `i` (caller's or sorted order).
+__device__ __forceinline__ int seg_of_index(const SegDesc *__restrict__ seg, int B, int64_t i)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (seg[m].base <= i) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
+
+// A size known only on the device (an edge or chain count): kernels read
+// *dev when it is set, so a captured graph needs no host round trip; `max`
+// bounds it and sizes the grid.
+struct DevCount {
+    int64_t max;
+    const uint32_t *dev;
+    __device__ __forceinline__ int64_t get() const
+    {
+        if (!dev) return max;
+        const int64_t v = (int64_t)*dev;
+        return v < max ? v : max;
+    }
+};
+
 // ------------------------------------------------------------ launches ---
 // sort.cu
 int scan_exclusive_u32(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *total_dev);
+int scan_exclusive_u32_dev(hop_ctx *c, const uint32_t *in, uint32_t *out, DevCount n,
+                           uint32_t *total_dev);
 size_t radix_sort_scratch_bytes(int64_t n);
+int radix_sort_u64_dev(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
+                       uint32_t *&vals_alt, DevCount n, int begin_bit, int end_bit, void *scratch);
 int radix_sort_u64(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
                    uint32_t *&vals_alt, int64_t n, int begin_bit, int end_bit, void *scratch);
 int iota_u32(hop_ctx *c, uint32_t *out, int64_t n);
@@ -163,6 +246,16 @@ int chunk_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint3
 int chunk_features(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
                    int level_dense, int64_t n, bool f64, double box, int qpw, float *feat,
                    uint8_t *lvl, const float *rk_s, float *target);
+
+// grid.cu, mlp.cu: batched pass (subvolume descriptors on the device)
+int grid_build_seg(hop_ctx *c, const float *pos, int64_t n, const SegDesc *seg, int B,
+                   int64_t n_cells, void **spos_out, uint32_t **perm_out, uint64_t **keys_out,
+                   uint32_t **cellT_out);
+int chunk_feat_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r,
+                   float *feat, uint8_t *lvl);
+int mlp_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r);
 
 // knn.cu
 struct KnnArgs {
@@ -180,6 +273,9 @@ struct KnnArgs {
     uint32_t *nbr_s;           // n x ld_out sorted indices, or nullptr
     float *dens_s;             // n
     float *rk_s;               // n or nullptr
+    const SegDesc *seg = nullptr;   // batched pass: subvolume descriptors (device)
+    int B = 0;                      // number of subvolumes
+    int64_t n_chunks = 0;           // batched pass: total query chunks
 };
 int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr);
 
@@ -190,12 +286,42 @@ int hop_links(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int
 int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr,
                      int ld, int64_t n, int n_merge, float delta_outer,
                      uint64_t **edge_key, double **edge_sum, int64_t *n_edges);
+int hop_links_async(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
+                    int n_hop, uint32_t *hop, uint32_t *chain);
+int boundaries_table_async(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey,
+                           const uint32_t *nbr, int ld, int64_t n, int n_merge, float delta_outer,
+                           int64_t cap, uint32_t *m_dev, unsigned long long *nins,
+                           uint64_t **edge_key, double **edge_sum);
 int gather_f64(hop_ctx *c, const double *src, const uint32_t *idx, int64_t n, double *dst);
 int scatter_outputs(hop_ctx *c, const uint32_t *perm, int64_t n, const float *dens_s, float *dens,
                     const int32_t *group_s, int32_t *group, const uint32_t *nbr_s, int ld_s,
                     uint32_t *nbr, int ld, int n_cols, const uint32_t *chain_s, uint32_t *chain);
 
 // merge.cu
+struct MergeGraphArgs {
+    const uint32_t *chain;      // n chain labels (sorted order)
+    const uint64_t *dkey;       // n density keys
+    int64_t n;
+    const uint64_t *edge_key;   // boundary pairs, count on the device
+    const double *edge_sum;
+    DevCount m;                 // edge count (max = table capacity)
+    float d_o, d_s, d_p;
+    const SegDesc *seg;         // subvolumes (device), B >= 1
+    int B;
+    int32_t *group;             // n: group rank within the subvolume, -1 = none
+    uint32_t *n_groups;         // B (device): groups per subvolume
+    uint32_t *counts;           // 8 device words: chains, groups, loop flag, rounds (2)
+};
+int merge_groups_graph(hop_ctx *c, const MergeGraphArgs &a);
+
+// batch.cu: a device-bounded loop.  Captured, it becomes a conditional
+// while node whose body `body` enqueues; otherwise the host repeats it.
+// The body sets *changed (a device word, zero on entry) to ask for another
+// round; more than max_rounds rounds set err_bit in the error word.
+void batch_free(hop_ctx *c);   // drops the cached graph and its buffers
+int graph_while(hop_ctx *c, uint32_t *changed, uint32_t *round, int max_rounds, uint32_t err_bit,
+                int (*body)(hop_ctx *, void *), void *arg);
+
 int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_t n,
                  const uint64_t *edge_key, const double *edge_sum, int64_t n_edges,
                  float delta_outer, float delta_saddle, float delta_peak,

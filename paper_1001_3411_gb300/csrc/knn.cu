@@ -364,6 +364,8 @@ template <typename T> struct KnnDev {
     float plain_r;
     int cpr;
     T norm;                       // box^3 / (n pi)
+    const SegDesc *seg;           // subvolumes of a batched pass (SEG kernels)
+    int B;
     uint32_t *nbr_s;
     float *dens_s;
     float *rk_s;
@@ -442,7 +444,9 @@ __device__ __forceinline__ bool in_cube(const int *c, int rx, int ry, int rz, in
            (((rz - c[2]) % G + G) % G) < c[5];
 }
 
-template <typename T, int P>
+// SEG: a batched pass over subvolumes; each chunk takes its box, cell table,
+// radius and density normalisation from its subvolume's descriptor.
+template <typename T, int P, bool SEG>
 __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
 {
     using L = WarpSmem<T, P>;
@@ -473,7 +477,6 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
     T *od = (T *)(wbase + L::od(a.buf)) + q * OCAP;
     uint32_t *os = (uint32_t *)(wbase + L::os(a.buf)) + q * OCAP;
 
-    const T box = a.box, half = a.half_box, inv_box = a.inv_box;
     const int k = a.k;
     unsigned long long cand_acc = 0, search_acc = 0, retry_acc = 0, warp_acc = 0;
 
@@ -483,8 +486,36 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
         ch = __shfl_sync(FULL, ch, 0);
         if ((int64_t)ch >= a.n_chunks) break;
         ++warp_acc;
-        const int64_t s_first = (int64_t)ch * Q;
-        const int nq = (int)min((int64_t)Q, a.n - s_first);
+        int64_t s_first, n_end, seg_base;
+        T box, half, inv_box, norm;
+        const uint32_t *cellT;
+        int level_dense;
+        float plain_r;
+        if constexpr (SEG) {
+            const SegDesc &sd = a.seg[seg_of_chunk(a.seg, a.B, (int64_t)ch)];
+            seg_base = sd.base;
+            n_end = sd.base + sd.n;
+            s_first = sd.base + ((int64_t)ch - sd.chunk0) * Q;
+            box = (T)sd.box;
+            half = (T)(0.5 * sd.box);
+            inv_box = (T)(1.0 / sd.box);
+            norm = (T)sd.norm;
+            cellT = a.cellT + sd.cell0;
+            level_dense = sd.level_dense;
+            plain_r = sd.plain_r;
+        } else {
+            seg_base = 0;
+            n_end = a.n;
+            s_first = (int64_t)ch * Q;
+            box = a.box;
+            half = a.half_box;
+            inv_box = a.inv_box;
+            norm = a.norm;
+            cellT = a.cellT;
+            level_dense = a.level_dense;
+            plain_r = a.plain_r;
+        }
+        const int nq = (int)min((int64_t)Q, n_end - s_first);
         const bool active = q < nq;
         const int64_t sq = s_first + (active ? q : 0);
         const typename V4<T>::type qv = a.spos[sq];
@@ -496,7 +527,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
         }
         __syncwarp();
 
-        T R = a.chunk_r ? (T)a.chunk_r[ch] : (T)a.plain_r;
+        T R = a.chunk_r ? (T)a.chunk_r[ch] : (T)plain_r;
         if (!(R > T(0))) R = box * T(1e-6);
         T tau = R * R;
         int cnt = 0;
@@ -604,7 +635,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                     uint32_t ra = 0, rb = 0;
                     const int ci = cb + lane;
                     if (full) {
-                        if (lane == 0) { ra = 0; rb = (uint32_t)a.n; }
+                        if (lane == 0) { ra = (uint32_t)seg_base; rb = (uint32_t)n_end; }
                     } else if (ci < ncells) {
                         const int ix = c0x + ci % nx, iy = c0y + (ci / nx) % ny, iz = c0z + ci / (nx * ny);
                         const int rx = ((ix % G) + G) % G, ry = ((iy % G) + G) % G, rz = ((iz % G) + G) % G;
@@ -627,7 +658,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                         }
                         if (keep) {
                             const uint64_t code = morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz);
-                            cell_range(a.cellT, a.keys, a.level_dense, l, code, ra, rb);
+                            cell_range(cellT, a.keys, level_dense, l, code, ra, rb);
                         }
                     }
                     uint32_t len = rb - ra, inc = len;
@@ -948,7 +979,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                 float dens;
                 if (vk > T(0)) {
                     const T h = rk * T(0.5);
-                    dens = (float)(a.norm * ((T)wsum * T(2.3283064365386963e-10)) / (h * h * h));
+                    dens = (float)(norm * ((T)wsum * T(2.3283064365386963e-10)) / (h * h * h));
                 } else {
                     dens = INFINITY;
                 }
@@ -968,7 +999,7 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
 
 template <typename T, int P> size_t knn_smem_per_warp(int buf) { return WarpSmem<T, P>::total(buf); }
 
-template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
+template <typename T, int P, bool SEG> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
 {
     constexpr int Q = 32 / P;
     KnnDev<T> d;
@@ -977,7 +1008,9 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     d.cellT = a.cellT;
     d.level_dense = a.level_dense;
     d.n = a.n;
-    d.n_chunks = (a.n + Q - 1) / Q;
+    d.n_chunks = SEG ? a.n_chunks : (a.n + Q - 1) / Q;
+    d.seg = a.seg;
+    d.B = a.B;
     d.box = (T)a.box;
     d.inv_box = (T)(1.0 / a.box);
     d.half_box = (T)(0.5 * a.box);
@@ -985,8 +1018,9 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     d.n_out = a.n_out;
     d.ld_out = a.ld_out;
     // room for 4 Ndens entries per query (3 with 8 or more queries per warp,
-    // where the larger buffer would cost a resident block): compactions are rare
-    d.cap = (Q <= 4 ? 4 : 3) * a.k;
+    // where the larger buffer would cost a resident block): compactions are
+    // rare.  A tuned context may set 2, 3 or 4.
+    d.cap = (c->capf ? c->capf : (Q <= 4 ? 4 : 3)) * a.k;
     d.buf = d.cap + 4 * P + 4;
     d.chunk_r = a.chunk_r;
     d.plain_r = a.plain_r;
@@ -1008,7 +1042,7 @@ template <typename T, int P> int knn_run(hop_ctx *c, const KnnArgs &a, int cpr)
     if (per_warp * warps > (size_t)max_smem)
         return ctx_fail(c, HOP_EINVAL, "kNN search buffer does not fit in shared memory");
     const size_t smem = per_warp * warps;
-    auto kern = knn_kernel<T, P>;
+    auto kern = knn_kernel<T, P, SEG>;
     HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
@@ -1028,13 +1062,23 @@ int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr)
 {
     if (a.k < 2 || a.k > kMaxDens) return ctx_fail(c, HOP_EINVAL, "n_dens out of range");
     if (cpr < 1 || cpr > 4) cpr = 1;
+    if (a.seg) {
+        // batched passes: float32 positions, 4, 8 or 16 queries per warp
+        if (f64) return ctx_fail(c, HOP_EINVAL, "batched passes take float32 positions");
+        switch (qpw) {
+        case 16: return knn_run<float, 2, true>(c, a, cpr);
+        case 8: return knn_run<float, 4, true>(c, a, cpr);
+        case 4: return knn_run<float, 8, true>(c, a, cpr);
+        default: return ctx_fail(c, HOP_EINVAL, "batched passes take 4, 8 or 16 queries per warp");
+        }
+    }
     switch (qpw) {
-    case 32: return f64 ? knn_run<double, 1>(c, a, cpr) : knn_run<float, 1>(c, a, cpr);
-    case 16: return f64 ? knn_run<double, 2>(c, a, cpr) : knn_run<float, 2>(c, a, cpr);
-    case 8: return f64 ? knn_run<double, 4>(c, a, cpr) : knn_run<float, 4>(c, a, cpr);
-    case 4: return f64 ? knn_run<double, 8>(c, a, cpr) : knn_run<float, 8>(c, a, cpr);
-    case 2: return f64 ? knn_run<double, 16>(c, a, cpr) : knn_run<float, 16>(c, a, cpr);
-    case 1: return f64 ? knn_run<double, 32>(c, a, cpr) : knn_run<float, 32>(c, a, cpr);
+    case 32: return f64 ? knn_run<double, 1, false>(c, a, cpr) : knn_run<float, 1, false>(c, a, cpr);
+    case 16: return f64 ? knn_run<double, 2, false>(c, a, cpr) : knn_run<float, 2, false>(c, a, cpr);
+    case 8: return f64 ? knn_run<double, 4, false>(c, a, cpr) : knn_run<float, 4, false>(c, a, cpr);
+    case 4: return f64 ? knn_run<double, 8, false>(c, a, cpr) : knn_run<float, 8, false>(c, a, cpr);
+    case 2: return f64 ? knn_run<double, 16, false>(c, a, cpr) : knn_run<float, 16, false>(c, a, cpr);
+    case 1: return f64 ? knn_run<double, 32, false>(c, a, cpr) : knn_run<float, 32, false>(c, a, cpr);
     default: return ctx_fail(c, HOP_EINVAL, "queries per warp must be 1, 2, 4, 8, 16 or 32");
     }
 }

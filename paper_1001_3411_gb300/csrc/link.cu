@@ -322,6 +322,53 @@ int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, co
     return ctx_fail(c, HOP_ENOMEM, "boundary table could not be sized");
 }
 
+// Graph-safe forms (no host round trip): errors go to the context's error
+// word, which the caller reads once the pass has run.
+int hop_links_async(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
+                    int n_hop, uint32_t *hop, uint32_t *chain)
+{
+    hop_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, nbr, ld, n, n_hop, hop, chain, c->d_err);
+    HOP_LAUNCH(c);
+    chain_halving_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, n, c->d_err);
+    HOP_LAUNCH(c);
+    chain_root_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, n, c->d_err);
+    HOP_LAUNCH(c);
+    chain_check_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(hop, chain, n, c->d_err);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+// Boundary table of fixed capacity `cap` (a power of two).  The edge count
+// lands in *m_dev; edge_key / edge_sum hold cap entries, the first *m_dev
+// valid.  An overfull table sets kErrTableFull in the error word.
+int boundaries_table_async(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey,
+                           const uint32_t *nbr, int ld, int64_t n, int n_merge, float delta_outer,
+                           int64_t cap, uint32_t *m_dev, unsigned long long *nins,
+                           uint64_t **edge_key, double **edge_sum)
+{
+    uint64_t *hkey = (uint64_t *)ctx_buf(c, S_HKEY, cap * sizeof(uint64_t));
+    unsigned long long *hval = (unsigned long long *)ctx_buf(c, S_HVAL, cap * sizeof(uint64_t));
+    uint32_t *occ = (uint32_t *)ctx_buf(c, S_EDGE_TMP, (cap + 1) * sizeof(uint32_t));
+    uint64_t *ek = (uint64_t *)ctx_buf(c, S_EDGE_KEY, cap * sizeof(uint64_t));
+    double *es = (double *)ctx_buf(c, S_EDGE_SUM, cap * sizeof(double));
+    if (!hkey || !hval || !occ || !ek || !es) return HOP_ENOMEM;
+    fill_u64_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, cap, kEmpty);
+    HOP_LAUNCH(c);
+    HOP_CUDA(c, cudaMemsetAsync(hval, 0, cap * sizeof(uint64_t), c->stream));
+    boundary_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, nbr, ld, n, n_merge, delta_outer,
+                                                          hkey, hval, (uint64_t)cap - 1, c->d_err, nins);
+    HOP_LAUNCH(c);
+    occupied_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, cap, occ);
+    HOP_LAUNCH(c);
+    int rc = scan_exclusive_u32(c, occ, occ, cap, m_dev);
+    if (rc) return rc;
+    compact_table_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, hval, cap, occ, ek, es);
+    HOP_LAUNCH(c);
+    *edge_key = ek;
+    *edge_sum = es;
+    return HOP_OK;
+}
+
 int gather_f64(hop_ctx *c, const double *src, const uint32_t *idx, int64_t n, double *dst)
 {
     gather_f64_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(src, idx, n, dst);

@@ -41,10 +41,11 @@ __device__ __forceinline__ float mlp_forward_one(const float *W, const float *x,
 }
 
 // out[s] = MLP(feat[s]); with lvl != null the output is the search radius
-// side(lvl) * exp(y + margin) instead.
+// side(lvl) * exp(y + margin) instead, and with side != null it is
+// side[s] * exp(y + margin) (side may alias out).
 __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const float *__restrict__ feat,
-                               int64_t m, float *__restrict__ out, const uint8_t *__restrict__ lvl,
-                               double box, float margin)
+                               int64_t m, float *out, const uint8_t *__restrict__ lvl,
+                               double box, float margin, const float *side)
 {
     __shared__ float W[NP];
     for (int i = threadIdx.x; i < NP; i += blockDim.x) W[i] = bf(w16, i);
@@ -55,9 +56,11 @@ __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const floa
 #pragma unroll
         for (int f = 0; f < IN; ++f) x[f] = feat[s * IN + f];
         const float y = mlp_forward_one(W, x, h1);
-        if (lvl) {
-            const float side = (float)(box / (double)(1u << lvl[s]));
-            out[s] = side * expf(y + margin);
+        if (side) {
+            out[s] = side[s] * expf(y + margin);
+        } else if (lvl) {
+            const float sd = (float)(box / (double)(1u << lvl[s]));
+            out[s] = sd * expf(y + margin);
         } else {
             out[s] = y;
         }
@@ -191,7 +194,7 @@ int grad_launch(hop_ctx *c, const float *feat, const float *target, const uint32
     blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 2);
     blocks = std::max<int64_t>(blocks, 1);
     mlp_grad_kernel<<<(unsigned)blocks, kGradThreads, smem, c->stream>>>(
-        (const __nv_bfloat16 *)c->mlp.w16, feat, target, idx, m, scale, grad, loss);
+        (const __nv_bfloat16 *)c->mlp->w16, feat, target, idx, m, scale, grad, loss);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -200,31 +203,33 @@ int grad_launch(hop_ctx *c, const float *feat, const float *target, const uint32
 
 int mlp_ensure(hop_ctx *c)
 {
-    if (c->mlp.w32) return HOP_OK;
+    if (c->mlp->w32) return HOP_OK;
     char *p = nullptr;
     const size_t bytes = sizeof(float) * NP * 4 + sizeof(uint16_t) * NP + 256;
     HOP_CUDA(c, cudaMalloc(&p, bytes));
     HOP_CUDA(c, cudaMemset(p, 0, bytes));
-    c->mlp.w32 = (float *)p;
-    c->mlp.m = c->mlp.w32 + NP;
-    c->mlp.v = c->mlp.m + NP;
-    c->mlp.g = c->mlp.v + NP;
-    c->mlp.w16 = (uint16_t *)(c->mlp.g + NP);
+    c->mlp->w32 = (float *)p;
+    c->mlp->m = c->mlp->w32 + NP;
+    c->mlp->v = c->mlp->m + NP;
+    c->mlp->g = c->mlp->v + NP;
+    c->mlp->w16 = (uint16_t *)(c->mlp->g + NP);
     return HOP_OK;
 }
 
 void mlp_free(hop_ctx *c)
 {
-    if (c->mlp.w32) cudaFree(c->mlp.w32);
-    c->mlp = MlpState();
+    for (MlpState &m : c->mlp_bank) {
+        if (m.w32) cudaFree(m.w32);
+        m = MlpState();
+    }
 }
 
 int mlp_forward_dev(hop_ctx *c, const float *feat, int64_t m, float *out)
 {
     int64_t blocks = std::min<int64_t>((m + 127) / 128, (int64_t)c->num_sms * 8);
     blocks = std::max<int64_t>(blocks, 1);
-    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp.w16, feat, m,
-                                                           out, nullptr, 1.0, 0.f);
+    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat, m,
+                                                           out, nullptr, 1.0, 0.f, nullptr);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -241,8 +246,28 @@ int mlp_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_
     if (rc) return rc;
     int64_t blocks = std::min<int64_t>((nc + 127) / 128, (int64_t)c->num_sms * 8);
     blocks = std::max<int64_t>(blocks, 1);
-    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp.w16, feat, nc,
-                                                           chunk_r, lvl, p->box, c->mlp.log_margin);
+    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat, nc,
+                                                           chunk_r, lvl, p->box, c->mlp->log_margin, nullptr);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+// Batched pass: features of every chunk (with the cell side of its own
+// subvolume in chunk_r), then radius = side * exp(MLP + margin) in place.
+int mlp_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r)
+{
+    if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no radius network loaded (hop_mlp_load)");
+    float *feat = (float *)ctx_buf(c, S_MLP_TMP, n_chunks * IN * sizeof(float));
+    uint8_t *lvl = (uint8_t *)ctx_buf(c, S_CHUNK_LVL, n_chunks);
+    if (!feat || !lvl) return HOP_ENOMEM;
+    int rc = chunk_feat_seg(c, spos, keys, cellT, seg, B, n_chunks, qpw, k, chunk_r, feat, lvl);
+    if (rc) return rc;
+    int64_t blocks = std::min<int64_t>((n_chunks + 127) / 128, (int64_t)c->num_sms * 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat,
+                                                           n_chunks, chunk_r, nullptr, 1.0,
+                                                           c->mlp->log_margin, chunk_r);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -255,22 +280,22 @@ int hop_mlp_load(hop_ctx *c, const float *params_host, float log_margin)
     HOP_CUDA(c, cudaSetDevice(c->device));
     int rc = mlp_ensure(c);
     if (rc) return rc;
-    HOP_CUDA(c, cudaMemcpyAsync(c->mlp.w32, params_host, sizeof(float) * NP, cudaMemcpyHostToDevice, c->stream));
-    HOP_CUDA(c, cudaMemsetAsync(c->mlp.m, 0, sizeof(float) * NP * 2, c->stream));
-    to_bf16_kernel<<<8, 256, 0, c->stream>>>(c->mlp.w32, (__nv_bfloat16 *)c->mlp.w16, NP);
+    HOP_CUDA(c, cudaMemcpyAsync(c->mlp->w32, params_host, sizeof(float) * NP, cudaMemcpyHostToDevice, c->stream));
+    HOP_CUDA(c, cudaMemsetAsync(c->mlp->m, 0, sizeof(float) * NP * 2, c->stream));
+    to_bf16_kernel<<<8, 256, 0, c->stream>>>(c->mlp->w32, (__nv_bfloat16 *)c->mlp->w16, NP);
     HOP_LAUNCH(c);
     HOP_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->mlp.loaded = true;
-    c->mlp.log_margin = log_margin;
-    c->mlp.step = 0;
+    c->mlp->loaded = true;
+    c->mlp->log_margin = log_margin;
+    c->mlp->step = 0;
     return HOP_OK;
 }
 
 int hop_mlp_get(hop_ctx *c, float *params_host)
 {
     if (!c || !params_host) return HOP_EINVAL;
-    if (!c->mlp.loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
-    HOP_CUDA(c, cudaMemcpyAsync(params_host, c->mlp.w32, sizeof(float) * NP, cudaMemcpyDeviceToHost, c->stream));
+    if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
+    HOP_CUDA(c, cudaMemcpyAsync(params_host, c->mlp->w32, sizeof(float) * NP, cudaMemcpyDeviceToHost, c->stream));
     HOP_CUDA(c, cudaStreamSynchronize(c->stream));
     return HOP_OK;
 }
@@ -296,7 +321,7 @@ int hop_mlp_samples(hop_ctx *c, float *feat, float *target, int64_t cap, int64_t
 int hop_mlp_forward(hop_ctx *c, const float *feat, int64_t m, float *out)
 {
     if (!c || !feat || !out || m < 0) return HOP_EINVAL;
-    if (!c->mlp.loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
+    if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
     HOP_CUDA(c, cudaSetDevice(c->device));
     if (m == 0) return HOP_OK;
     return mlp_forward_dev(c, feat, m, out);
@@ -306,7 +331,7 @@ int hop_mlp_grad(hop_ctx *c, const float *feat, const float *target, int64_t m, 
                  float *grad)
 {
     if (!c || !feat || !target || !grad || !loss || m <= 0) return HOP_EINVAL;
-    if (!c->mlp.loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
+    if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no network loaded");
     HOP_CUDA(c, cudaSetDevice(c->device));
     double *dl = (double *)ctx_buf(c, S_MISC, 256);
     if (!dl) return HOP_ENOMEM;
@@ -324,7 +349,7 @@ int hop_mlp_train(hop_ctx *c, const float *feat, const float *target, int64_t m,
                   int32_t batch, float lr, uint64_t seed, double *final_loss)
 {
     if (!c || !feat || !target || m <= 0 || epochs <= 0 || batch <= 0) return HOP_EINVAL;
-    if (!c->mlp.loaded) return ctx_fail(c, HOP_ENOMODEL, "load initial parameters first (hop_mlp_load)");
+    if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "load initial parameters first (hop_mlp_load)");
     HOP_CUDA(c, cudaSetDevice(c->device));
     uint32_t *perm = (uint32_t *)ctx_buf(c, S_MLP_TMP, m * sizeof(uint32_t));
     double *dl = (double *)ctx_buf(c, S_MISC, 256);
@@ -346,15 +371,15 @@ int hop_mlp_train(hop_ctx *c, const float *feat, const float *target, int64_t m,
         HOP_CUDA(c, cudaMemsetAsync(dl, 0, sizeof(double), c->stream));
         for (int64_t b = 0; b < m; b += batch) {
             const int64_t bs = std::min<int64_t>(batch, m - b);
-            HOP_CUDA(c, cudaMemsetAsync(c->mlp.g, 0, sizeof(float) * NP, c->stream));
+            HOP_CUDA(c, cudaMemsetAsync(c->mlp->g, 0, sizeof(float) * NP, c->stream));
             // loss of each batch is its mean; weight it by bs/m for the epoch mean
-            int rc = grad_launch(c, feat, target, perm + b, bs, 1.f / (float)bs, c->mlp.g, dl);
+            int rc = grad_launch(c, feat, target, perm + b, bs, 1.f / (float)bs, c->mlp->g, dl);
             if (rc) return rc;
-            c->mlp.step += 1;
-            const float bc1 = 1.f - powf(0.9f, (float)c->mlp.step);
-            const float bc2 = 1.f - powf(0.999f, (float)c->mlp.step);
-            adam_kernel<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->mlp.w32, (__nv_bfloat16 *)c->mlp.w16,
-                                                                c->mlp.m, c->mlp.v, c->mlp.g, lr, bc1, bc2);
+            c->mlp->step += 1;
+            const float bc1 = 1.f - powf(0.9f, (float)c->mlp->step);
+            const float bc2 = 1.f - powf(0.999f, (float)c->mlp->step);
+            adam_kernel<<<(NP + 255) / 256, 256, 0, c->stream>>>(c->mlp->w32, (__nv_bfloat16 *)c->mlp->w16,
+                                                                c->mlp->m, c->mlp->v, c->mlp->g, lr, bc1, bc2);
             HOP_LAUNCH(c);
         }
         HOP_CUDA(c, cudaMemcpyAsync(c->h_pinned, dl, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -55,10 +55,11 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *smem_warp, uint32
     return r;
 }
 
-__global__ void scan_reduce_kernel(const uint32_t *__restrict__ in, int64_t n,
+__global__ void scan_reduce_kernel(const uint32_t *__restrict__ in, DevCount nc,
                                    uint32_t *__restrict__ partial)
 {
     __shared__ uint32_t sw[33];
+    const int64_t n = nc.get();
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t s = 0;
 #pragma unroll
@@ -73,10 +74,11 @@ __global__ void scan_reduce_kernel(const uint32_t *__restrict__ in, int64_t n,
 
 // Each thread owns kScanItems consecutive items.
 __global__ void scan_apply_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                  int64_t n, const uint32_t *__restrict__ partial_scanned,
+                                  DevCount nc, const uint32_t *__restrict__ partial_scanned,
                                   uint32_t *__restrict__ total_dev, int write_total)
 {
     __shared__ uint32_t sw[33];
+    const int64_t n = nc.get();
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -101,10 +103,11 @@ __global__ void scan_apply_kernel(const uint32_t *__restrict__ in, uint32_t *__r
 
 // ------------------------------------------------------------ radix sort --
 
-__global__ void radix_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, int shift,
+__global__ void radix_hist_kernel(const uint64_t *__restrict__ keys, DevCount nc, int shift,
                                   int64_t nblocks, uint32_t *__restrict__ counts)
 {
     __shared__ uint32_t hist[256];
+    const int64_t n = nc.get();
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -127,9 +130,10 @@ __global__ void radix_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, 
 __global__ void radix_scatter_kernel(const uint64_t *__restrict__ keys_in,
                                      const uint32_t *__restrict__ vals_in,
                                      uint64_t *__restrict__ keys_out,
-                                     uint32_t *__restrict__ vals_out, int64_t n, int shift,
+                                     uint32_t *__restrict__ vals_out, DevCount nc, int shift,
                                      int64_t nblocks, const uint32_t *__restrict__ offsets)
 {
+    const int64_t n = nc.get();
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[kSortWarps][256];
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
@@ -189,10 +193,10 @@ static size_t scan_scratch_elems(int64_t n)
     return tot + 64;
 }
 
-static int scan_rec(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
+static int scan_rec(hop_ctx *c, const uint32_t *in, uint32_t *out, DevCount n, uint32_t *scratch,
                     uint32_t *total_dev)
 {
-    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    const int64_t nb = (n.max + kScanTile - 1) / kScanTile;
     if (nb <= 1) {
         scan_apply_kernel<<<1, kScanThreads, 0, c->stream>>>(in, out, n, nullptr, total_dev, 1);
         HOP_LAUNCH(c);
@@ -201,7 +205,7 @@ static int scan_rec(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n, ui
     uint32_t *partial = scratch;
     scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(in, n, partial);
     HOP_LAUNCH(c);
-    int rc = scan_rec(c, partial, partial, nb, scratch + nb + 64, total_dev);
+    int rc = scan_rec(c, partial, partial, DevCount{nb, nullptr}, scratch + nb + 64, total_dev);
     if (rc) return rc;
     scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(in, out, n, partial, nullptr, 0);
     HOP_LAUNCH(c);
@@ -211,11 +215,18 @@ static int scan_rec(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n, ui
 int scan_exclusive_u32(hop_ctx *c, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *total_dev)
 {
-    if (n <= 0) {
+    return scan_exclusive_u32_dev(c, in, out, DevCount{n, nullptr}, total_dev);
+}
+
+// Items [0, n.get()) are scanned; the grid covers n.max.
+int scan_exclusive_u32_dev(hop_ctx *c, const uint32_t *in, uint32_t *out, DevCount n,
+                           uint32_t *total_dev)
+{
+    if (n.max <= 0) {
         if (total_dev) HOP_CUDA(c, cudaMemsetAsync(total_dev, 0, 4, c->stream));
         return HOP_OK;
     }
-    uint32_t *scratch = (uint32_t *)ctx_buf(c, S_SCAN, scan_scratch_elems(n) * sizeof(uint32_t));
+    uint32_t *scratch = (uint32_t *)ctx_buf(c, S_SCAN, scan_scratch_elems(n.max) * sizeof(uint32_t));
     if (!scratch) return HOP_ENOMEM;
     return scan_rec(c, in, out, n, scratch, total_dev);
 }
@@ -233,7 +244,18 @@ int radix_sort_u64(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&
                    uint32_t *&vals_alt, int64_t n, int begin_bit, int end_bit, void *scratch)
 {
     if (n <= 1) return HOP_OK;
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    return radix_sort_u64_dev(c, keys, keys_alt, vals, vals_alt, DevCount{n, nullptr}, begin_bit,
+                              end_bit, scratch);
+}
+
+// Sorts the first n.get() pairs; the grid and the scratch cover n.max.  The
+// number of passes is fixed by the bit range, so the result lands in the
+// same buffer whatever the device count.
+int radix_sort_u64_dev(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_t *&vals,
+                       uint32_t *&vals_alt, DevCount n, int begin_bit, int end_bit, void *scratch)
+{
+    if (n.max <= 0) return HOP_OK;
+    const int64_t nb = (n.max + kSortTile - 1) / kSortTile;
     uint32_t *counts = (uint32_t *)scratch;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, c->stream>>>(keys, n, shift, nb, counts);
