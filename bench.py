@@ -3,10 +3,13 @@
 
 One step is one complete HOP pass (cell build, kNN + density, hops, chains,
 boundaries, merge, results in the caller's order) over the 512^3 synthetic
-NFW + 40% background box.  The headline value uses the learned first search
-radius; the plain-radius path is timed beside it and must give identical
-output.  Inputs are resident in HBM for `value`; `e2e` passes host (pinned)
-buffers through the same C-ABI call, copies included.
+NFW + 40% background box, through the batched call (one subvolume, the pass
+captured once into a CUDA graph and replayed).  The headline value uses the
+learned first search radius; the plain-radius path is timed beside it and
+must give identical output.  Inputs are resident in HBM for `value`; `e2e`
+passes host (pinned) buffers through the same C-ABI call, copies included.
+The `batch` object times the 64-subvolume workload (graph pass, the same
+pass enqueued kernel by kernel, and one hop_run per subvolume).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -45,6 +48,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="override particle count (testing)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-subvolume section")
     return ap.parse_args()
 
 
@@ -169,34 +173,21 @@ def oracle_rate(pos, seconds: float, seed: int = 7):
 
 
 # ------------------------------------------------------------- gb300 arm
-def tune(hop, dpos, params, out, candidates):
-    """Untimed: pick the fastest (queries per warp, cells per radius) for a
-    radius policy; output does not depend on it."""
-    import torch
-    best = None
-    for qpw, cpr in candidates:
-        hop.set_tuning(qpw, cpr)
-        if params.radius_mode == 2:
-            load_model(hop, qpw)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hop.hop_run(dpos, params, out=out)
-        t = time.perf_counter() - t0
-        if best is None or t < best[0]:
-            best = (t, qpw, cpr)
-    return best
-
-
 _MODELS = None
 
 
-def load_model(hop, qpw):
+def load_models(hop):
+    """Loads the stored network of every queries-per-warp setting into the
+    context (one network per setting)."""
     global _MODELS
     from paper_1001_3411_gb300 import radius_model
     if _MODELS is None:
         _MODELS = radius_model.load()
-    params, margin = _MODELS[qpw]
-    hop.hop_mlp_load(params, margin)
+    saved = hop.get_tuning()
+    for q, (params, margin) in _MODELS.items():
+        hop.set_tuning(q, 1)
+        hop.hop_mlp_load(params, margin)
+    hop.apply_tuning(saved["qpw"], saved["cpr"], saved["buf_factor"])
 
 
 def ensure_model(hop):
@@ -221,7 +212,9 @@ def ensure_model(hop):
     return "trained now"
 
 
-def timed_steps(hop, dpos, params, out, steps, dist):
+def timed(fn, steps, dist, hop):
+    """Runs fn() `steps` times between CUDA events on torch's current stream
+    (the stream the library enqueues on), barrier + synchronize around."""
     import torch
     st = torch.cuda.current_stream()
     stats = []
@@ -232,13 +225,76 @@ def timed_steps(hop, dpos, params, out, steps, dist):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(steps):
-        hop.hop_run(dpos, params, out=out)
+        fn()
         stats.append(hop.stats())
     e1.record(st)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    return e0.elapsed_time(e1), stats
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, stats
+
+
+def stage(st):
+    keys = ("ms_sort", "ms_radius", "ms_knn", "ms_link", "ms_boundaries", "ms_merge", "ms_total")
+    return {k[3:]: round(statistics.median(s[k] for s in st), 3) for k in keys}
+
+
+CANDS = {"learned": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (4, 1, 3)],
+         "count": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0)],
+         "plain": [(4, 1, 0), (8, 1, 0)]}
+
+
+def batch_section(hop, args, dist):
+    """The 64-subvolume workload (N_b log-uniform in [16^3, 128^3], NFW + 30%
+    background): one graph-captured batched pass against the same pass
+    enqueued kernel by kernel and against one hop_run call per subvolume."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1001_3411_gb300 import default_params
+    pos, off = synth.workload("batch64")
+    B = len(off) - 1
+    n = int(off[-1])
+    boxes = np.ones(B)
+    d = torch.from_numpy(pos).cuda()
+    subs = [d[off[b]:off[b + 1]] for b in range(B)]
+    out = {"group": torch.empty(n, dtype=torch.int32, device="cuda"),
+           "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
+    res = {"workload": "batch64", "n_subvolumes": B, "n_particles": n,
+           "sizes": [int(x) for x in (np.diff(off).min(), np.median(np.diff(off)), np.diff(off).max())]}
+    for name, mode in (("learned", 2), ("plain", 0)):
+        p = default_params(radius_mode=mode)
+        best, tr = hop.hop_autotune(d, off, boxes, p, CANDS[name], reps=2)
+        t = hop.get_tuning()
+        kinds = (("graph", lambda: hop.hop_run_batch(d, off, boxes, p, out=out)),)
+        if name == "learned":
+            kinds += (("eager", lambda: hop.hop_run_batch(d, off, boxes, p, out=out, eager=True)),
+                      ("per_subvolume", lambda: [hop.hop_run(sb, p) for sb in subs]))
+        r = {"tuning": [t["qpw"], t["cpr"], t["buf_factor"]],
+             "autotune_ms": {str(tuple(c)): round(x["ms"], 2) for c, x in zip(CANDS[name], tr)}}
+        for kind, fn in kinds:
+            for _ in range(args.warmup):
+                fn()
+            ms, st = timed(fn, args.steps, dist, hop)
+            r[kind] = {"value": n / (ms / args.steps * 1e-3), "ms_per_step": ms / args.steps}
+            if kind == "graph":
+                r[kind]["stages_ms"] = stage(st)
+                r[kind]["gpu_launches_per_step"] = int(st[-1]["launches"])
+                r[kind]["n_groups"] = int(st[-1]["n_groups"])
+        res[name] = r
+    res["speedup_graph_vs_per_subvolume"] = (res["learned"]["per_subvolume"]["ms_per_step"] /
+                                            res["learned"]["graph"]["ms_per_step"])
+    res["speedup_learned_vs_plain"] = (res["plain"]["graph"]["ms_per_step"] /
+                                      res["learned"]["graph"]["ms_per_step"])
+    del d, subs, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_gb300(args):
@@ -260,6 +316,7 @@ def run_gb300(args):
     build_library()
     hop = Hop(local)
     model_src = ensure_model(hop)
+    load_models(hop)
 
     if args.scale:
         pos, _ = synth.nfw_box(args.scale, synth.workload_seed(3, rank))
@@ -268,68 +325,76 @@ def run_gb300(args):
         pos = synth.workload(args.workload, sub=rank)
         wl = args.workload
     n = len(pos)
+    off, boxes = [0, n], [1.0]
     dpos = torch.from_numpy(pos).cuda()
     out = {"group": torch.empty(n, dtype=torch.int32, device="cuda"),
            "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
-    p_learn = default_params(radius_mode=2)
-    p_plain = default_params(radius_mode=0)
-    p_count = default_params(radius_mode=1)
-    cands = [(8, 1)] if args.no_tune else [(4, 1), (8, 1), (16, 1), (8, 2)]
+    params = {"learned": default_params(radius_mode=2), "plain": default_params(radius_mode=0),
+              "count": default_params(radius_mode=1)}
+    # the autotuner (graph replays, untimed) picks each policy's tuning;
+    # output does not depend on it
     tuned = {}
-    for name, p, cs in (("learned", p_learn, [c for c in cands if c[0] in (4, 8, 16)]),
-                        ("plain", p_plain, cands), ("count", p_count, cands)):
-        t, q, c = tune(hop, dpos, p, out, cs)
-        tuned[name] = (q, c)
+    for name in ("learned", "count", "plain"):
+        cs = CANDS[name][:1] if args.no_tune else CANDS[name]
+        best, tr = hop.hop_autotune(dpos, off, boxes, params[name], cs, reps=1)
+        tuned[name] = tuple(cs[best])
 
     def configure(name):
-        q, c = tuned[name]
-        hop.set_tuning(q, c)
-        if name == "learned":
-            load_model(hop, q)
+        hop.apply_tuning(*tuned[name])
+
+    def step(name):
+        return lambda: hop.hop_run_batch(dpos, off, boxes, params[name], out=out)
 
     # identical output across radius policies (untimed check)
     ref = {}
-    for name, p in (("plain", p_plain), ("learned", p_learn), ("count", p_count)):
+    for name in ("plain", "learned", "count"):
         configure(name)
-        r = hop.hop_run(dpos, p, out=out)
-        ref[name] = (out["group"].clone(), out["dens"].clone(), r["n_groups"])
+        r = hop.hop_run_batch(dpos, off, boxes, params[name], out=out)
+        ref[name] = (out["group"].clone(), out["dens"].clone(), int(r["n_groups"][0]))
     same = all(torch.equal(ref["plain"][0], ref[k][0]) and torch.equal(ref["plain"][1], ref[k][1])
                for k in ("learned", "count"))
 
     results = {}
-    for name, p in (("plain", p_plain), ("count", p_count), ("learned", p_learn)):
+    clocks = {}
+    for name in ("plain", "count", "learned"):
         configure(name)
         for _ in range(args.warmup):
-            hop.hop_run(dpos, p, out=out)
+            step(name)()
         if name == "learned":
             with ClockSampler(gpu_index(local)) as cs:
-                ms, stats = timed_steps(hop, dpos, p, out, args.steps, dist)
+                ms, stats = timed(step(name), args.steps, dist, hop)
             clocks = cs.summary()
         else:
-            ms, stats = timed_steps(hop, dpos, p, out, args.steps, dist)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms, stats = timed(step(name), args.steps, dist, hop)
         results[name] = (ms / args.steps, stats)
 
-    # end to end through the same C-ABI call with host buffers
+    # the single-volume call (hop_run, host round trips between stages) on
+    # the same box and tuning, for comparison
     configure("learned")
+    for _ in range(max(1, args.warmup - 1)):
+        hop.hop_run(dpos, params["learned"], out=out)
+    ms_single, _ = timed(lambda: hop.hop_run(dpos, params["learned"], out=out), args.steps, dist, hop)
+    ms_single /= args.steps
+
+    # end to end through the same C-ABI call with host (pinned) buffers
     hpos = torch.from_numpy(pos).pin_memory()
     hout = {"group": torch.empty(n, dtype=torch.int32).pin_memory(),
             "dens": torch.empty(n, dtype=torch.float32).pin_memory()}
-    hop.hop_run(hpos, p_learn, out=hout)
+    hop.hop_run_batch(hpos, off, boxes, params["learned"], out=hout)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        hop.hop_run(hpos, p_learn, out=hout)
+        hop.hop_run_batch(hpos, off, boxes, params["learned"], out=hout)
     e2e_s = (time.perf_counter() - t0) / args.steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     assert torch.equal(hout["group"], ref["plain"][0].cpu()), "host-buffer run differs"
+    del hpos, hout
+
+    batch = batch_section(hop, args, dist) if not args.no_batch else None
 
     ms_l, st_l = results["learned"]
     ms_p, st_p = results["plain"]
@@ -343,10 +408,6 @@ def run_gb300(args):
     alg_flop = n * IDEAL_CANDIDATES * FLOP_PER_CANDIDATE
     achieved = alg_flop / (knn_ms * 1e-3) / 1e12
     tpp, tsrc = knn_traffic_per_particle()
-
-    def stage(st):
-        keys = ("ms_sort", "ms_radius", "ms_knn", "ms_link", "ms_boundaries", "ms_merge", "ms_total")
-        return {k[3:]: round(statistics.median(s[k] for s in st), 3) for k in keys}
 
     line = {
         "metric": METRIC,
@@ -363,13 +424,14 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": wl, "n_particles": n, "n_dens": N_DENS, "n_hop": N_HOP,
                    "n_merge": N_MERGE, "deltas": list(DELTAS), "radius": "learned",
+                   "path": "hop_run_batch (one subvolume), graph-captured pass",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs (12 B/particle, %.2f GB) larger than L2; no flush" % (n * 12 / 1e9),
-                   "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1]}
+                   "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1], "buf_factor": v[2]}
                               for k, v in tuned.items()},
                    "radius_model": model_src},
         "identical_output": bool(same),
-        "n_groups": int(ref["learned"][2]),
+        "n_groups": ref["learned"][2],
         "plain": {"value": n * world / (ms_p * 1e-3), "ms_per_step": ms_p, "stages_ms": stage(st_p),
                   "candidates_per_particle": st_p[-1]["candidates"] / n,
                   "retries": st_p[-1]["retries"], "searches": st_p[-1]["searches"]},
@@ -378,18 +440,21 @@ def run_gb300(args):
                   "retries": st_c[-1]["retries"], "searches": st_c[-1]["searches"]},
         "learned": {"stages_ms": stage(st_l), "candidates_per_particle": last["candidates"] / n,
                     "retries": last["retries"], "searches": last["searches"]},
+        "single_call_hop_run": {"value": n * world / (ms_single * 1e-3), "ms_per_step": ms_single},
         "speedup_learned_vs_plain": ms_p / ms_l,
-        "roofline": {"kernel": "knn_kernel<float,P> (kNN + M4 density)", "bound": "alu",
+        "roofline": {"kernel": "knn_kernel<float,P,SEG> (kNN + M4 density)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": (tpp * n if tpp else None),
                      "traffic_basis": tsrc,
                      "basis": ("algorithmic flop = N x 64 x 6/pi candidates x 8 flop; peak = SMs x 128 "
                                "FP32 lanes x 2 x sampled median SM clock"),
                      "knn_ms": knn_ms},
-        "gpu_launches": int(last["launches"]),
+        "gpu_launches": int(sum(s["launches"] for s in st_l)),
+        "gpu_launches_per_step": int(last["launches"]),
         "clocks": clocks,
         "e2e": {"value": n * world / e2e_s, "unit": "particles/s",
                 "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 8},
+        "batch": batch,
     }
     if rank == 0:
         line["cpu_baseline"] = oracle_rate(pos, args.cpu_seconds)
