@@ -2,10 +2,13 @@
 times and counters: a small driver for profilers (ncu) and quick timing.
 
   python -m paper_1001_3411_gb300.run_case --n 16777216 --radius learned \
-      --qpw 4 --cpr 1 --steps 2 [--path batch|single]
+      --qpw 4 --cpr 1 --steps 2 [--path batch|eager|single]
 
 ``--path batch`` (the default) runs the box as a one-subvolume batched pass
-(the CUDA-graph path the benchmark times); ``--path single`` calls hop_run.
+(the CUDA-graph path the benchmark times); ``--path eager`` runs the same
+pass with its kernels enqueued one by one (the same kernels on the same
+data; profilers that cannot look inside a graph with conditional nodes see
+them this way); ``--path single`` calls hop_run.
 
 The box is the NFW + 40% background generator with the 512^3 workload's
 seed (``synth.nfw_box``), so any --n is a smaller copy of the benchmark box.
@@ -33,7 +36,7 @@ def main(argv=None):
     ap.add_argument("--qpw", type=int, default=4)
     ap.add_argument("--cpr", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--path", choices=["batch", "single"], default="batch")
+    ap.add_argument("--path", choices=["batch", "eager", "single"], default="batch")
     a = ap.parse_args(argv)
     build_library()
     pos, _ = synth.nfw_box(a.n, synth.workload_seed(3))
@@ -46,8 +49,8 @@ def main(argv=None):
         h.hop_mlp_load(w, m)
     p = default_params(radius_mode=mode)
     for i in range(a.steps):
-        if a.path == "batch":
-            h.hop_run_batch(d, [0, a.n], [1.0], p)
+        if a.path in ("batch", "eager"):
+            h.hop_run_batch(d, [0, a.n], [1.0], p, eager=a.path == "eager")
         else:
             h.hop_run(d, p)
         print(json.dumps(dict(step=i, **h.stats())), flush=True)
