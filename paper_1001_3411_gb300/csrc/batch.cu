@@ -354,8 +354,8 @@ int check_batch_params(hop_ctx *c, const hop_params *p)
         return ctx_fail(c, HOP_EINVAL, "unknown radius_mode");
     if (p->radius_mode == HOP_RADIUS_LEARNED && !c->mlp->loaded)
         return ctx_fail(c, HOP_ENOMODEL, "no radius network loaded for this queries-per-warp setting");
-    if (c->qpw != 4 && c->qpw != 8 && c->qpw != 16)
-        return ctx_fail(c, HOP_EINVAL, "batched passes take 4, 8 or 16 queries per warp");
+    if (c->qpw != 4 && c->qpw != 8 && c->qpw != 16 && c->qpw != 32)
+        return ctx_fail(c, HOP_EINVAL, "batched passes take 4, 8, 16 or 32 queries per warp");
     return HOP_OK;
 }
 
@@ -559,8 +559,8 @@ int hop_get_tuning(const hop_ctx *c, hop_tuning *out)
 int hop_apply_tuning(hop_ctx *c, const hop_tuning *t)
 {
     if (!c || !t) return HOP_EINVAL;
-    if (t->buf_factor != 0 && (t->buf_factor < 2 || t->buf_factor > 4))
-        return ctx_fail(c, HOP_EINVAL, "buffer factor must be 0 (default), 2, 3 or 4");
+    if (t->buf_factor != 0 && (t->buf_factor < 2 || t->buf_factor > 6))
+        return ctx_fail(c, HOP_EINVAL, "buffer factor must be 0 (default) or 2 to 6");
     const int rc = hop_set_tuning(c, t->qpw, t->cpr);
     if (rc) return rc;
     c->capf = t->buf_factor;
@@ -586,7 +586,7 @@ int hop_autotune(hop_ctx *c, const float *pos, const int64_t *offsets, const dou
     float best_ms = 0.f;
     for (int i = 0; i < n_cand && rc == HOP_OK; ++i) {
         cand[i].ms = -1.f;
-        if (cand[i].qpw != 4 && cand[i].qpw != 8 && cand[i].qpw != 16) continue;
+        if (cand[i].qpw != 4 && cand[i].qpw != 8 && cand[i].qpw != 16 && cand[i].qpw != 32) continue;
         if (hop_apply_tuning(c, &cand[i]) != HOP_OK) continue;
         if (p && p->radius_mode == HOP_RADIUS_LEARNED && !c->mlp->loaded) continue;
         // the first run captures the pass; the timed ones replay it

@@ -278,6 +278,7 @@ struct KnnArgs {
     int64_t n_chunks = 0;           // batched pass: total query chunks
 };
 int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr);
+int knn32_launch(hop_ctx *c, const KnnArgs &a, int cpr);   // knn32.cu: one query per lane, float32
 
 // link.cu
 int make_dkey(hop_ctx *c, const float *dens, const uint32_t *orig, int64_t n, uint64_t *dkey);

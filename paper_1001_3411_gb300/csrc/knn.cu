@@ -30,6 +30,7 @@
 // kernel weights, so results do not depend on R, on the radius policy or on
 // the order candidates arrive in.
 #include "hop_internal.cuh"
+#include "knn_common.cuh"
 
 #include <math.h>
 
@@ -53,49 +54,6 @@ template <> __device__ __forceinline__ uint32_t orig_of<float>(const float4 &v) 
 template <> __device__ __forceinline__ uint32_t orig_of<double>(const double4 &v)
 {
     return (uint32_t)__double_as_longlong(v.w);
-}
-
-// 1/8-octave bin of v relative to tau's own bin: bins 0..31, bin 31 holds
-// tau's octave-eighth, lower bins smaller values; bin 0 also holds everything
-// below.  Monotone in v for v >= 0.
-__device__ __forceinline__ int bin_base(float tau) { return (int)(__float_as_uint(tau) >> 20); }
-__device__ __forceinline__ int bin_base(double tau)
-{
-    return (int)((unsigned long long)__double_as_longlong(tau) >> 49);
-}
-__device__ __forceinline__ int bin_of(float v, int tb)
-{
-    int b = (int)(__float_as_uint(v) >> 20) - tb + (kHistBins - 1);
-    return min(max(b, 0), kHistBins - 1);
-}
-__device__ __forceinline__ int bin_of(double v, int tb)
-{
-    int b = (int)((unsigned long long)__double_as_longlong(v) >> 49) - tb + (kHistBins - 1);
-    return min(max(b, 0), kHistBins - 1);
-}
-// Largest value whose bin is <= b (b < 31), or -1 if that is below zero.
-__device__ __forceinline__ float bin_upper(float, int tb, int b)
-{
-    int e = tb - (kHistBins - 1) + b + 1;
-    if (e <= 0) return -1.f;
-    return __uint_as_float(((uint32_t)e << 20) - 1u);
-}
-__device__ __forceinline__ double bin_upper(double, int tb, int b)
-{
-    long long e = (long long)tb - (kHistBins - 1) + b + 1;
-    if (e <= 0) return -1.0;
-    return __longlong_as_double((long long)(((unsigned long long)e << 49) - 1ull));
-}
-
-// M4 cubic spline w(q) (Monaghan & Lattanzio 1985): W = w(r/h) / (pi h^3).
-template <typename T> __device__ __forceinline__ T m4(T q)
-{
-    if (q < T(1)) return T(1) - T(1.5) * q * q + T(0.75) * q * q * q;
-    if (q < T(2)) {
-        T t = T(2) - q;
-        return T(0.25) * t * t * t;
-    }
-    return T(0);
 }
 
 constexpr int KCAP = 32;   // entries of the k-th entry's bin ranked exactly in a small list
@@ -373,47 +331,6 @@ template <typename T> struct KnnDev {
     unsigned long long *counters;
     uint32_t *err;
 };
-
-// Contiguous range of sorted particles in level-l cell `code`.
-__device__ __forceinline__ void cell_range(const uint32_t *__restrict__ cellT,
-                                           const uint64_t *__restrict__ keys, int Ld, int l,
-                                           uint64_t code, uint32_t &a, uint32_t &b)
-{
-    if (l <= Ld) {
-        const int sh = 3 * (Ld - l);
-        a = cellT[code << sh];
-        b = cellT[(code + 1) << sh];
-        return;
-    }
-    const int up = 3 * (l - Ld);
-    const uint64_t pc = code >> up;
-    uint32_t lo = cellT[pc], hi = cellT[pc + 1];
-    const int ksh = 3 * (kMaxLevel - l);
-    const uint64_t k0 = code << ksh, k1 = (code + 1) << ksh;
-    // lower_bound(k0)
-    uint32_t L = lo, H = hi;
-    while (L < H) {
-        uint32_t m = (L + H) >> 1;
-        if (keys[m] < k0) L = m + 1; else H = m;
-    }
-    a = L;
-    H = hi;
-    while (L < H) {
-        uint32_t m = (L + H) >> 1;
-        if (keys[m] < k1) L = m + 1; else H = m;
-    }
-    b = L;
-}
-
-template <typename T> __device__ __forceinline__ T wrapdiff(T xj, T xi, T box, T half)
-{
-    // Minimum-image difference with one rounding: the coordinate >= L/2 of
-    // the pair is moved by -L (exact) when the plain difference exceeds L/2.
-    T d = xj - xi;
-    if (d > half) return (xj - box) - xi;
-    if (d < -half) return xj - (xi - box);
-    return d;
-}
 
 // Shared-memory layout of one warp (byte offsets), used by kernel and host.
 template <typename T, int P> struct WarpSmem {
@@ -1062,14 +979,15 @@ int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr)
 {
     if (a.k < 2 || a.k > kMaxDens) return ctx_fail(c, HOP_EINVAL, "n_dens out of range");
     if (cpr < 1 || cpr > 4) cpr = 1;
+    if (qpw == 32 && !f64) return knn32_launch(c, a, cpr);   // one query per lane
     if (a.seg) {
-        // batched passes: float32 positions, 4, 8 or 16 queries per warp
+        // batched passes: float32 positions, 4, 8, 16 or 32 queries per warp
         if (f64) return ctx_fail(c, HOP_EINVAL, "batched passes take float32 positions");
         switch (qpw) {
         case 16: return knn_run<float, 2, true>(c, a, cpr);
         case 8: return knn_run<float, 4, true>(c, a, cpr);
         case 4: return knn_run<float, 8, true>(c, a, cpr);
-        default: return ctx_fail(c, HOP_EINVAL, "batched passes take 4, 8 or 16 queries per warp");
+        default: return ctx_fail(c, HOP_EINVAL, "batched passes take 4, 8, 16 or 32 queries per warp");
         }
     }
     switch (qpw) {

@@ -89,13 +89,20 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_PATH)
     ap.add_argument("--n", type=int, default=256 ** 3, help="training set size (NFW + 40%% background)")
-    ap.add_argument("--qpw", default="4,8,16")
+    ap.add_argument("--qpw", default="4,8,16,32")
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--merge", action="store_true",
+                    help="keep the stored networks of the other queries-per-warp settings")
     args = ap.parse_args()
     pos, _ = synth.nfw_box(args.n, synth.workload_seed(2))
     dpos = torch.from_numpy(pos).cuda()
     hop = Hop(0)
     models, meta = {}, {"train_n": args.n, "workload": "nfw256" if args.n == 256 ** 3 else "nfw"}
+    if args.merge and os.path.exists(args.out):
+        models.update(load(args.out))
+        z = np.load(args.out)
+        if "meta" in z.files:
+            meta["previous"] = str(z["meta"])
     for q in [int(x) for x in args.qpw.split(",")]:
         feat, tgt = samples(hop, dpos, q)
         params, margin, st = train(hop, feat, tgt, epochs=args.epochs)
