@@ -244,9 +244,12 @@ def stage(st):
     return {k[3:]: round(statistics.median(s[k] for s in st), 3) for k in keys}
 
 
-CANDS = {"learned": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (4, 1, 3)],
-         "count": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0)],
-         "plain": [(4, 1, 0), (8, 1, 0)]}
+CANDS = {"learned": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (4, 1, 3), (32, 1, 0), (32, 1, 3)],
+         "count": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (32, 1, 3)],
+         "plain": [(4, 1, 0), (8, 1, 0), (32, 1, 0), (32, 1, 3)]}
+# boxes of 2^29 particles or more run through hop_run (the batched pass sizes
+# its merge arrays by the particle count) with these fixed tunings
+FIXED = {"learned": (4, 1, 0), "count": (4, 1, 0), "plain": (32, 1, 3)}
 
 
 def batch_section(hop, args, dist):
@@ -331,10 +334,14 @@ def run_gb300(args):
            "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
     params = {"learned": default_params(radius_mode=2), "plain": default_params(radius_mode=0),
               "count": default_params(radius_mode=1)}
+    single = n >= (1 << 29)
     # the autotuner (graph replays, untimed) picks each policy's tuning;
     # output does not depend on it
     tuned = {}
     for name in ("learned", "count", "plain"):
+        if single:
+            tuned[name] = FIXED[name]
+            continue
         cs = CANDS[name][:1] if args.no_tune else CANDS[name]
         best, tr = hop.hop_autotune(dpos, off, boxes, params[name], cs, reps=1)
         tuned[name] = tuple(cs[best])
@@ -342,16 +349,22 @@ def run_gb300(args):
     def configure(name):
         hop.apply_tuning(*tuned[name])
 
-    def step(name):
-        return lambda: hop.hop_run_batch(dpos, off, boxes, params[name], out=out)
+    def call(name, pos_in, o):
+        if single:
+            return int(hop.hop_run(pos_in, params[name], out=o)["n_groups"])
+        return int(hop.hop_run_batch(pos_in, off, boxes, params[name], out=o)["n_groups"][0])
 
-    # identical output across radius policies (untimed check)
+    def step(name):
+        return lambda: call(name, dpos, out)
+
+    # identical output across radius policies (untimed check): group ids
+    # compared whole, density bits through their sum
     ref = {}
     for name in ("plain", "learned", "count"):
         configure(name)
-        r = hop.hop_run_batch(dpos, off, boxes, params[name], out=out)
-        ref[name] = (out["group"].clone(), out["dens"].clone(), int(r["n_groups"][0]))
-    same = all(torch.equal(ref["plain"][0], ref[k][0]) and torch.equal(ref["plain"][1], ref[k][1])
+        ng = call(name, dpos, out)
+        ref[name] = (out["group"].clone(), int(out["dens"].view(torch.int32).sum(dtype=torch.int64)), ng)
+    same = all(torch.equal(ref["plain"][0], ref[k][0]) and ref["plain"][1:] == ref[k][1:]
                for k in ("learned", "count"))
 
     results = {}
@@ -371,21 +384,24 @@ def run_gb300(args):
     # the single-volume call (hop_run, host round trips between stages) on
     # the same box and tuning, for comparison
     configure("learned")
-    for _ in range(max(1, args.warmup - 1)):
-        hop.hop_run(dpos, params["learned"], out=out)
-    ms_single, _ = timed(lambda: hop.hop_run(dpos, params["learned"], out=out), args.steps, dist, hop)
-    ms_single /= args.steps
+    if single:
+        ms_single = results["learned"][0]
+    else:
+        for _ in range(max(1, args.warmup - 1)):
+            hop.hop_run(dpos, params["learned"], out=out)
+        ms_single, _ = timed(lambda: hop.hop_run(dpos, params["learned"], out=out), args.steps, dist, hop)
+        ms_single /= args.steps
 
     # end to end through the same C-ABI call with host (pinned) buffers
     hpos = torch.from_numpy(pos).pin_memory()
     hout = {"group": torch.empty(n, dtype=torch.int32).pin_memory(),
             "dens": torch.empty(n, dtype=torch.float32).pin_memory()}
-    hop.hop_run_batch(hpos, off, boxes, params["learned"], out=hout)
+    call("learned", hpos, hout)
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        hop.hop_run_batch(hpos, off, boxes, params["learned"], out=hout)
+        call("learned", hpos, hout)
     e2e_s = (time.perf_counter() - t0) / args.steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
@@ -424,7 +440,8 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": wl, "n_particles": n, "n_dens": N_DENS, "n_hop": N_HOP,
                    "n_merge": N_MERGE, "deltas": list(DELTAS), "radius": "learned",
-                   "path": "hop_run_batch (one subvolume), graph-captured pass",
+                   "path": ("hop_run (single call; 2^29 particles or more)" if single else
+                            "hop_run_batch (one subvolume), graph-captured pass"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs (12 B/particle, %.2f GB) larger than L2; no flush" % (n * 12 / 1e9),
                    "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1], "buf_factor": v[2]}

@@ -3,6 +3,7 @@
 // "resorted" position copy, Parallel HOP Sec. 4 "kD-tree Speedup"), plus
 // per-chunk stencil counts used to pick first search radii.
 #include "hop_internal.cuh"
+#include "chunk_stencil.cuh"
 
 #include <math.h>
 
@@ -118,34 +119,6 @@ __global__ void cell_table_seg_kernel(const uint64_t *__restrict__ keys, int64_t
     }
 }
 
-__device__ __forceinline__ void cell_range_g(const uint32_t *__restrict__ cellT,
-                                             const uint64_t *__restrict__ keys, int Ld, int l,
-                                             uint64_t code, uint32_t &a, uint32_t &b)
-{
-    if (l <= Ld) {
-        const int sh = 3 * (Ld - l);
-        a = cellT[code << sh];
-        b = cellT[(code + 1) << sh];
-        return;
-    }
-    const uint64_t pc = code >> (3 * (l - Ld));
-    uint32_t lo = cellT[pc], hi = cellT[pc + 1];
-    const int ksh = 3 * (kMaxLevel - l);
-    const uint64_t k0 = code << ksh, k1 = (code + 1) << ksh;
-    uint32_t L = lo, H = hi;
-    while (L < H) {
-        uint32_t m = (L + H) >> 1;
-        if (keys[m] < k0) L = m + 1; else H = m;
-    }
-    a = L;
-    H = hi;
-    while (L < H) {
-        uint32_t m = (L + H) >> 1;
-        if (keys[m] < k1) L = m + 1; else H = m;
-    }
-    b = L;
-}
-
 // One warp per chunk of Q sorted particles: the chunk's level (cell side
 // just >= its bounding-box extent) and the particle counts of the 3x3x3
 // cells around the cell holding the box centre.  Writes, as requested:
@@ -170,56 +143,14 @@ __global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t ch = warp0; ch < n_chunks; ch += nwarps) {
-        int64_t s0 = ch * Q, n = n_all;
-        const uint32_t *cellT = cellT_all;
-        int Ld = Ld_all;
-        T box = box_all, inv_box = inv_box_all;
-        if (seg) {
-            const SegDesc &d = seg[seg_of_chunk(seg, B, ch)];
-            s0 = d.base + (ch - d.chunk0) * Q;
-            n = d.base + d.n;
-            cellT = cellT_all + d.cell0;
-            Ld = d.level_dense;
-            box = (T)d.box;
-            inv_box = (T)(1.0 / d.box);
-        }
-        const int nq = (int)min((int64_t)Q, n - s0);
-        const int64_t s = s0 + (lane < nq ? lane : 0);
-        const typename V4<T>::type v = spos[s];
-        T lx = v.x, ly = v.y, lz = v.z, hx = v.x, hy = v.y, hz = v.z;
-        float rk = (rk_s && lane < nq) ? rk_s[s] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = min(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-            ly = min(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-            lz = min(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-            hx = max(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-            hy = max(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-            hz = max(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-            rk = fmaxf(rk, __shfl_xor_sync(0xffffffffu, rk, o));
-        }
-        const T ext = max(hx - lx, max(hy - ly, hz - lz));
-        int l = kMaxLevel;
-        while (l > 2 && box / (T)(1 << l) < ext) --l;
-        const int G = 1 << l;
-        const T sc = inv_box * (T)G;
-        const int cx = min((int)floor((lx + hx) * T(0.5) * sc), G - 1);
-        const int cy = min((int)floor((ly + hy) * T(0.5) * sc), G - 1);
-        const int cz = min((int)floor((lz + hz) * T(0.5) * sc), G - 1);
-        uint32_t cnt = 0;
-        if (lane < 27) {
-            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-            const int rx = (cx + dx + G) % G, ry = (cy + dy + G) % G, rz = (cz + dz + G) % G;
-            uint32_t a, b;
-            cell_range_g(cellT, keys, Ld, l, morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz), a, b);
-            cnt = b - a;
-            if (feat) feat[ch * HOP_MLP_IN + lane] = log1pf((float)cnt);
-        }
-        uint32_t tot = cnt;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        uint32_t cnt, tot;
+        int l;
+        double side;
+        float rk;
+        chunk_stencil<T>((const typename Vec4<T>::type *)spos, keys, cellT_all, Ld_all, n_all, Q, box_all,
+                         inv_box_all, seg, B, ch, rk_s, lane, cnt, tot, l, side, rk);
+        if (feat && lane < 27) feat[ch * HOP_MLP_IN + lane] = log1pf((float)cnt);
         if (lane == 0) {
-            const double side = (double)box / (double)G;
             if (lvl) lvl[ch] = (uint8_t)l;
             if (side_out) side_out[ch] = (float)side;
             if (chunk_r) {

@@ -4,6 +4,7 @@
 // Weights are BF16 (an fp32 master copy is kept for training); products and
 // sums are FP32.  Forward, backward and Adam are hand-written here.
 #include "hop_internal.cuh"
+#include "chunk_stencil.cuh"
 
 #include <cuda_bf16.h>
 
@@ -64,6 +65,48 @@ __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const floa
         } else {
             out[s] = y;
         }
+    }
+}
+
+// The learned first radius of every chunk in one pass: a warp computes the
+// 27 log-counts of 32 chunks into shared memory (one chunk at a time, 27
+// lanes looking up one stencil cell each), then each lane runs the network
+// for one of them: R = side * exp(MLP + margin).  Same arithmetic as the
+// feature kernel followed by mlp_fwd_kernel, without the features' round
+// trip through HBM.
+constexpr int kRadWarps = 4;
+__global__ void __launch_bounds__(kRadWarps * 32)
+radius_mlp_kernel(const __nv_bfloat16 *__restrict__ w16, const float4 *__restrict__ spos,
+                  const uint64_t *__restrict__ keys, const uint32_t *__restrict__ cellT, int Ld,
+                  int64_t n, int64_t n_chunks, int Q, float box, float inv_box,
+                  const SegDesc *__restrict__ seg, int B, float margin, float *__restrict__ chunk_r)
+{
+    __shared__ float W[NP];
+    __shared__ float F[kRadWarps][32][IN + 1];
+    __shared__ float S[kRadWarps][32];
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) W[i] = bf(w16, i);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * kRadWarps * 32;
+    for (int64_t base = ((int64_t)blockIdx.x * kRadWarps + w) * 32; base < n_chunks; base += stride) {
+        const int nc = (int)min((int64_t)32, n_chunks - base);
+        for (int j = 0; j < nc; ++j) {
+            uint32_t cnt, tot;
+            int l;
+            double side;
+            float rk;
+            chunk_stencil<float>(spos, keys, cellT, Ld, n, Q, box, inv_box, seg, B, base + j, nullptr, lane,
+                                 cnt, tot, l, side, rk);
+            if (lane < IN) F[w][j][lane] = log1pf((float)cnt);
+            if (lane == 0) S[w][j] = (float)side;
+        }
+        __syncwarp();
+        if (lane < nc) {
+            float h1[H];
+            const float y = mlp_forward_one(W, F[w][lane], h1);
+            chunk_r[base + lane] = S[w][lane] * expf(y + margin);
+        }
+        __syncwarp();
     }
 }
 
@@ -234,10 +277,28 @@ int mlp_forward_dev(hop_ctx *c, const float *feat, int64_t m, float *out)
     return HOP_OK;
 }
 
+namespace {
+
+int radius_fused(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld,
+                 int64_t n, int64_t n_chunks, int qpw, double box, const SegDesc *seg, int B, float *chunk_r)
+{
+    int64_t blocks = (n_chunks + kRadWarps * 32 - 1) / (kRadWarps * 32);
+    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    radius_mlp_kernel<<<(unsigned)blocks, kRadWarps * 32, 0, c->stream>>>(
+        (const __nv_bfloat16 *)c->mlp->w16, (const float4 *)spos, keys, cellT, Ld, n, n_chunks, qpw,
+        (float)box, (float)(1.0 / box), seg, B, c->mlp->log_margin, chunk_r);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+}  // namespace
+
 int mlp_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld,
                int64_t n, const hop_params *p, int qpw, float *chunk_r)
 {
     const int64_t nc = (n + qpw - 1) / qpw;
+    if (!p->pos_is_f64) return radius_fused(c, spos, keys, cellT, Ld, n, nc, qpw, p->box, nullptr, 0, chunk_r);
     float *feat = (float *)ctx_buf(c, S_MLP_TMP, nc * IN * sizeof(float));
     uint8_t *lvl = (uint8_t *)ctx_buf(c, S_CHUNK_LVL, nc);
     if (!feat || !lvl) return HOP_ENOMEM;
@@ -258,18 +319,8 @@ int mlp_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uin
                    const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r)
 {
     if (!c->mlp->loaded) return ctx_fail(c, HOP_ENOMODEL, "no radius network loaded (hop_mlp_load)");
-    float *feat = (float *)ctx_buf(c, S_MLP_TMP, n_chunks * IN * sizeof(float));
-    uint8_t *lvl = (uint8_t *)ctx_buf(c, S_CHUNK_LVL, n_chunks);
-    if (!feat || !lvl) return HOP_ENOMEM;
-    int rc = chunk_feat_seg(c, spos, keys, cellT, seg, B, n_chunks, qpw, k, chunk_r, feat, lvl);
-    if (rc) return rc;
-    int64_t blocks = std::min<int64_t>((n_chunks + 127) / 128, (int64_t)c->num_sms * 8);
-    blocks = std::max<int64_t>(blocks, 1);
-    mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat,
-                                                           n_chunks, chunk_r, nullptr, 1.0,
-                                                           c->mlp->log_margin, chunk_r);
-    HOP_LAUNCH(c);
-    return HOP_OK;
+    (void)k;
+    return radius_fused(c, spos, keys, cellT, 0, 0, n_chunks, qpw, 1.0, seg, B, chunk_r);
 }
 
 extern "C" {
