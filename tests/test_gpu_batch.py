@@ -28,7 +28,7 @@ def hop():
     hopgpu.build_library()
     h = hopgpu.Hop(0)
     models = radius_model.load()
-    for q in (4, 8, 16):
+    for q in (4, 8, 16, 32):
         h.set_tuning(q, 1)
         w, m = models[q]
         h.hop_mlp_load(w, m)
@@ -165,11 +165,11 @@ def test_autotune_applies_the_fastest_candidate(hop):
     p = hopgpu.default_params(radius_mode=hopgpu.HOP_RADIUS_LEARNED)
     hop.set_tuning(8, 1)
     before = hop.hop_run_batch(d, off, boxes, p)
-    cands = [(4, 1, 0), (8, 1, 0), (16, 1, 0), (8, 2, 0), (4, 1, 3), (32, 1, 0)]
+    cands = [(4, 1, 0), (8, 1, 0), (16, 1, 0), (8, 2, 0), (4, 1, 3), (2, 1, 0), (32, 1, 0)]
     best, res = hop.hop_autotune(d, off, boxes, p, cands, reps=3)
-    assert res[5]["ms"] == -1.0                       # 32 queries per warp: not a batched setting
+    assert res[5]["ms"] == -1.0                       # 2 queries per warp: not a batched setting
     timed = [i for i, t in enumerate(res) if t["ms"] >= 0]
-    assert len(timed) == 5
+    assert len(timed) == 6
     assert best == min(timed, key=lambda i: res[i]["ms"])
     t = hop.get_tuning()
     assert (t["qpw"], t["cpr"], t["buf_factor"]) == cands[best]
@@ -194,7 +194,7 @@ def test_batch_argument_errors(hop):
     bad[600, 1] = 1.0                                            # on the box face of subvolume 1
     with pytest.raises(hopgpu.HopError, match="HOP_EINVAL"):
         hop.hop_run_batch(torch.from_numpy(bad).cuda(), off, boxes, p)
-    hop.set_tuning(32, 1)
+    hop.set_tuning(1, 1)                                         # 1 query per warp: not a batched setting
     with pytest.raises(hopgpu.HopError, match="HOP_EINVAL"):
         hop.hop_run_batch(d, off, boxes, p)
     hop.set_tuning(2, 1)
