@@ -8,7 +8,7 @@ particles) through ctypes; the library is compiled with gcc on first use.
 
 Functions follow HOP as restated in Parallel HOP (arXiv:1001.3411), Sec. 2:
 ``knn`` (C1), ``density`` (C2), ``link`` (C3, C4), ``boundaries`` (C5),
-``merge`` (C6, C7) and ``hop`` (all of them).  Every function is pinned by
+``merge`` (C6, C7), ``halo_stats`` (C8, Sec. 3) and ``hop`` (C1-C7).  Every function is pinned by
 ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -52,9 +52,10 @@ def _L():
             lib.orc_link.argtypes = [vp, vp, i32, i64, i32, vp, vp]
             lib.orc_boundaries.argtypes = [vp, vp, vp, i32, i64, i32, dbl, vp, vp, vp, i64, vp]
             lib.orc_merge.argtypes = [vp, vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp, vp]
+            lib.orc_halo_stats.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp, vp, vp]
             lib.orc_set_threads.argtypes = [C.c_int]
             for f in ("orc_knn", "orc_density", "orc_link", "orc_boundaries", "orc_merge",
-                      "orc_num_threads"):
+                      "orc_halo_stats", "orc_num_threads"):
                 getattr(lib, f).restype = C.c_int
             _lib = lib
     return _lib
@@ -147,6 +148,21 @@ def merge(chain, dens, lo, hi, s, delta_outer: float, delta_saddle: float, delta
                           float(delta_outer), float(delta_saddle), float(delta_peak),
                           _p(group), C.byref(ng)), "merge")
     return group, ng.value
+
+
+def halo_stats(pos, dens, group, n_groups: int, box: float = 1.0):
+    """C8: per group (count int64, peak int32, com [G, 3] fp64, rmax fp64)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    dens = np.ascontiguousarray(dens, dtype=np.float64)
+    group = np.ascontiguousarray(group, dtype=np.int32)
+    n = group.shape[0]
+    count = np.zeros(n_groups, dtype=np.int64)
+    peak = np.zeros(n_groups, dtype=np.int32)
+    com = np.zeros((n_groups, 3), dtype=np.float64)
+    rmax = np.zeros(n_groups, dtype=np.float64)
+    _check(_L().orc_halo_stats(_p(pos), _p(dens), _p(group), n, int(n_groups), float(box), _p(count),
+                               _p(peak), _p(com), _p(rmax)), "halo_stats")
+    return count, peak, com, rmax
 
 
 DEFAULTS = dict(n_dens=64, n_hop=16, n_merge=4, delta_outer=80.0, delta_saddle=200.0,

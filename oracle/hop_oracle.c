@@ -26,6 +26,8 @@
  *                  (step 5, Fig. 1).
  *   C7 labels      particles below delta_outer are in no halo (step 1);
  *                  groups are numbered by (peak density desc, peak index asc).
+ *   C8 halo stats  mass, centre of mass and maximum radius of every halo
+ *                  (Sec. 3, last paragraph of the merging description).
  *
  * Arithmetic: positions are taken as doubles (fp32 inputs promote exactly);
  * distances, kernel sums and boundary sums are fp64.  Densities handed in
@@ -404,4 +406,62 @@ int orc_merge(const int32_t *chain, const double *dens, int64_t n,
 done:
     free(peak); free(parent); free(owned); free(edges); free(rank); free(pk);
     return rc;
+}
+
+/*
+ * C8.  The statistical properties the paper computes for every halo once
+ * the halos are known: dark matter mass, centre of mass and maximum radius.
+ * Readings: particle masses are equal, so a halo's mass is its member
+ * count.  In the periodic box the centre of mass is taken about the halo's
+ * peak particle (its member with the greatest key: density, then smaller
+ * index): the members' minimum-image offsets from the peak are averaged and
+ * added to the peak's position, then wrapped into [0, box).  The maximum
+ * radius is the largest minimum-image distance from that centre to a member.
+ * Outputs for g < n_groups: count[g], peak[g], com[3g .. 3g+2], rmax[g].
+ * A group id >= n_groups is an error; ids < 0 are no halo.
+ */
+int orc_halo_stats(const double *pos, const double *dens, const int32_t *group, int64_t n,
+                   int64_t n_groups, double box, int64_t *count, int32_t *peak, double *com,
+                   double *rmax)
+{
+    if (!pos || !dens || !group || n < 0 || n_groups < 0 || !(box > 0)) return ORC_EINVAL;
+    if (n_groups == 0) return ORC_OK;
+    if (!count || !peak || !com || !rmax) return ORC_EINVAL;
+    double *sum = (double *)calloc((size_t)n_groups * 3, sizeof(double));
+    if (!sum) return ORC_ENOMEM;
+    for (int64_t g = 0; g < n_groups; ++g) { count[g] = 0; peak[g] = -1; rmax[g] = 0.0; }
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t g = group[i];
+        if (g < 0) continue;
+        if (g >= n_groups) { free(sum); return ORC_EINVAL; }
+        ++count[g];
+        if (peak[g] < 0 || key_greater(dens, (int32_t)i, peak[g])) peak[g] = (int32_t)i;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t g = group[i];
+        if (g < 0) continue;
+        for (int d = 0; d < 3; ++d)
+            sum[3 * g + d] += min_image(pos[3 * i + d] - pos[3 * (int64_t)peak[g] + d], box);
+    }
+    for (int64_t g = 0; g < n_groups; ++g) {
+        for (int d = 0; d < 3; ++d) {
+            double c = count[g] > 0 ? pos[3 * (int64_t)peak[g] + d] + sum[3 * g + d] / (double)count[g] : 0.0;
+            if (c < 0.0) c += box;
+            if (c >= box) c -= box;
+            com[3 * g + d] = c;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t g = group[i];
+        if (g < 0) continue;
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double dx = min_image(pos[3 * i + d] - com[3 * g + d], box);
+            r2 += dx * dx;
+        }
+        const double r = sqrt(r2);
+        if (r > rmax[g]) rmax[g] = r;
+    }
+    free(sum);
+    return ORC_OK;
 }
