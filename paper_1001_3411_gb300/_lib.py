@@ -30,7 +30,7 @@ EXPORTS = ["hop_default_params", "hop_create", "hop_destroy", "hop_set_stream", 
            "hop_set_tuning", "hop_density", "hop_link", "hop_boundaries", "hop_merge", "hop_run",
            "hop_get_stats", "hop_mlp_load", "hop_mlp_get", "hop_mlp_samples", "hop_mlp_forward",
            "hop_mlp_grad", "hop_mlp_train", "hop_link_static", "hop_run_batch", "hop_get_tuning",
-           "hop_apply_tuning", "hop_autotune"]
+           "hop_apply_tuning", "hop_autotune", "hop_halo_stats"]
 
 
 class HopParams(C.Structure):
@@ -103,6 +103,7 @@ def load_library(path: str = LIB):
             "hop_link_static": (C.c_int, [vp, vp, i32, i64, i32, vp, vp, vp]),
             "hop_run_batch": (C.c_int, [vp, vp, vp, vp, i32, P, vp, vp, vp, vp, i32, i32]),
             "hop_get_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
+            "hop_halo_stats": (C.c_int, [vp, vp, i32, vp, vp, i64, i64, f64, vp, vp, vp, vp]),
             "hop_apply_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
             "hop_autotune": (C.c_int, [vp, vp, vp, vp, i32, P, C.POINTER(HopTuning), i32, i32,
                                        C.POINTER(i32)]),
@@ -303,6 +304,26 @@ class Hop:
                                          _ptr(dens), _ptr(group), _ptr(ng), _ptr(nbr), ld_nbr or 0,
                                          HOP_BATCH_EAGER if eager else 0))
         return dict(dens=dens, group=group, n_groups=ng, nbr=nbr)
+
+    def hop_halo_stats(self, pos, dens, group, n_groups: int, box: float = 1.0):
+        """Per group: count (int64), peak index (int32), centre of mass
+        (n_groups x 3 float64), maximum radius (float64), as CUDA tensors."""
+        import torch
+        self._sync_stream()
+        n = pos.shape[0]
+        f64 = pos.dtype == torch.float64
+        _need(pos, torch.float64 if f64 else torch.float32, (n, 3), "pos")
+        _need(dens, torch.float32, (n,), "dens")
+        _need(group, torch.int32, (n,), "group")
+        dev = pos.device
+        G = int(n_groups)
+        count = torch.empty(max(G, 1), dtype=torch.int64, device=dev)
+        peak = torch.empty(max(G, 1), dtype=torch.int32, device=dev)
+        com = torch.empty((max(G, 1), 3), dtype=torch.float64, device=dev)
+        rmax = torch.empty(max(G, 1), dtype=torch.float64, device=dev)
+        self._check(self.L.hop_halo_stats(self.h, _ptr(pos), 1 if f64 else 0, _ptr(dens), _ptr(group), n, G,
+                                          float(box), _ptr(count), _ptr(peak), _ptr(com), _ptr(rmax)))
+        return count[:G], peak[:G], com[:G], rmax[:G]
 
     def get_tuning(self) -> dict:
         t = HopTuning()

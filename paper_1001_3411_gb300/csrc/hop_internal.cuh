@@ -55,6 +55,7 @@ enum Slot {
     S_ESORT_K0, S_ESORT_K1, S_ESORT_V0, S_ESORT_V1, S_ESORT_TMP,   // edge-list sort
     S_SEG,                              // subvolume descriptors of a batched pass
     S_BATCH,                            // per-pass arrays of a batched pass
+    S_HALO,                             // halo statistics scratch
     S_COUNT
 };
 
