@@ -261,16 +261,24 @@ def batch_section(hop, args, dist):
 
     import synth
     from paper_1001_3411_gb300 import default_params
+    from paper_1001_3411_gb300.shard import shard_subvolumes, subset
     pos, off = synth.workload("batch64")
+    n_all = int(off[-1])
+    world = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    # several ranks: each runs its balanced share of the subvolumes (no data
+    # crosses ranks); the step time is the slowest rank's
+    share = shard_subvolumes(np.diff(off), world)[rank]
+    pos, off, boxes = subset(pos, off, np.ones(len(off) - 1), share)
     B = len(off) - 1
     n = int(off[-1])
-    boxes = np.ones(B)
     d = torch.from_numpy(pos).cuda()
     subs = [d[off[b]:off[b + 1]] for b in range(B)]
     out = {"group": torch.empty(n, dtype=torch.int32, device="cuda"),
            "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
-    res = {"workload": "batch64", "n_subvolumes": B, "n_particles": n,
-           "sizes": [int(x) for x in (np.diff(off).min(), np.median(np.diff(off)), np.diff(off).max())]}
+    res = {"workload": "batch64", "n_subvolumes": 64, "n_particles": n_all,
+           "sizes": [int(x) for x in (np.diff(off).min(), np.median(np.diff(off)), np.diff(off).max())],
+           "ranks": world, "scaling": "strong (subvolumes shared out by particle count)" if world > 1 else None}
     for name, mode in (("learned", 2), ("plain", 0)):
         p = default_params(radius_mode=mode)
         best, tr = hop.hop_autotune(d, off, boxes, p, CANDS[name], reps=2)
@@ -285,7 +293,7 @@ def batch_section(hop, args, dist):
             for _ in range(args.warmup):
                 fn()
             ms, st = timed(fn, args.steps, dist, hop)
-            r[kind] = {"value": n / (ms / args.steps * 1e-3), "ms_per_step": ms / args.steps}
+            r[kind] = {"value": n_all / (ms / args.steps * 1e-3), "ms_per_step": ms / args.steps}
             if kind == "graph":
                 r[kind]["stages_ms"] = stage(st)
                 r[kind]["gpu_launches_per_step"] = int(st[-1]["launches"])
