@@ -389,6 +389,26 @@ def run_gb300(args):
             ms, stats = timed(step(name), args.steps, dist, hop)
         results[name] = (ms / args.steps, stats)
 
+    # halo statistics (mass, centre of mass, maximum radius) of the learned
+    # run's groups: HBM-bound passes, timed alone
+    configure("learned")
+    ng_l = call("learned", dpos, out)
+    halo = None
+    if ng_l > 0:
+        for _ in range(2):
+            hop.hop_halo_stats(dpos, out["dens"], out["group"], ng_l)
+        hms, _ = timed(lambda: hop.hop_halo_stats(dpos, out["dens"], out["group"], ng_l), args.steps, dist, hop)
+        hms /= args.steps
+        members = int((out["group"] >= 0).sum())
+        # group ids read in three passes; density and two position reads per member
+        hbytes = 12 * n + 28 * members
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        halo = {"ms": hms, "n_groups": ng_l, "members": members,
+                "roofline": {"bound": "hbm", "achieved": hbytes / (hms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": hbytes / (hms * 1e-3) / 1e9 / hbm, "traffic": None,
+                             "basis": "12 B per particle (group id, 3 passes) + 28 B per member "
+                                      "(density, position twice); peak = measured copy bandwidth"}}
+
     # the single-volume call (hop_run, host round trips between stages) on
     # the same box and tuning, for comparison
     configure("learned")
@@ -480,6 +500,7 @@ def run_gb300(args):
         "e2e": {"value": n * world / e2e_s, "unit": "particles/s",
                 "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 8},
         "batch": batch,
+        "halo_stats": halo,
     }
     if rank == 0:
         line["cpu_baseline"] = oracle_rate(pos, args.cpu_seconds)
