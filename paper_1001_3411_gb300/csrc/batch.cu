@@ -229,8 +229,7 @@ int enqueue_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const Pass
         chunk_r = (float *)ctx_buf(c, S_CHUNK_R, pl.n_chunks * sizeof(float));
         if (!chunk_r) return HOP_ENOMEM;
         if (p->radius_mode == HOP_RADIUS_COUNT)
-            rc = chunk_feat_seg(c, spos, keys, cellT, seg, pl.B, pl.n_chunks, c->qpw, p->n_dens, chunk_r,
-                                nullptr, nullptr);
+            rc = chunk_radius_seg(c, spos, keys, cellT, seg, pl.B, pl.n_chunks, c->qpw, p->n_dens, chunk_r);
         else
             rc = mlp_radius_seg(c, spos, keys, cellT, seg, pl.B, pl.n_chunks, c->qpw, p->n_dens, chunk_r);
         if (rc) return rc;

@@ -125,8 +125,7 @@ __global__ void cell_table_seg_kernel(const uint64_t *__restrict__ keys, int64_t
 //   feat[c][27] = log(1 + count), lvl[c], the closed-form radius
 //   R = side * (81 k / (4 pi sum counts))^(1/3) * exp(log_margin)
 //   (the radius of a ball holding k particles at the stencil's mean
-//   density), the cell side itself, and the training target
-//   log(max r_k over the chunk / side).
+//   density), and the training target log(max r_k over the chunk / side).
 // With seg set (a batched pass) each chunk uses its subvolume's box, cell
 // table and particle range.
 template <typename T>
@@ -137,7 +136,7 @@ __global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
                                   float log_margin, float *__restrict__ chunk_r,
                                   float *__restrict__ feat, uint8_t *__restrict__ lvl,
                                   const float *__restrict__ rk_s, float *__restrict__ target,
-                                  const SegDesc *__restrict__ seg, int B, float *__restrict__ side_out)
+                                  const SegDesc *__restrict__ seg, int B)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -152,7 +151,6 @@ __global__ void chunk_feat_kernel(const typename V4<T>::type *__restrict__ spos,
         if (feat && lane < 27) feat[ch * HOP_MLP_IN + lane] = log1pf((float)cnt);
         if (lane == 0) {
             if (lvl) lvl[ch] = (uint8_t)l;
-            if (side_out) side_out[ch] = (float)side;
             if (chunk_r) {
                 const double r = side * cbrt(81.0 * k / (4.0 * 3.14159265358979323846 * (double)max(tot, 1u)));
                 chunk_r[ch] = (float)(r * exp((double)log_margin));
@@ -206,7 +204,7 @@ int chunk_feat_launch(hop_ctx *c, const void *spos, const uint64_t *keys, const 
     if (blocks < 1) blocks = 1;
     chunk_feat_kernel<T><<<(unsigned)blocks, 256, 0, c->stream>>>(
         (const typename V4<T>::type *)spos, keys, cellT, Ld, n, n_chunks, qpw, (T)box,
-        (T)(1.0 / box), k, log_margin, chunk_r, feat, lvl, rk_s, target, nullptr, 0, nullptr);
+        (T)(1.0 / box), k, log_margin, chunk_r, feat, lvl, rk_s, target, nullptr, 0);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -280,20 +278,16 @@ int grid_build_seg(hop_ctx *c, const float *pos, int64_t n, const SegDesc *seg, 
     return HOP_OK;
 }
 
-// Per-chunk features of a batched pass.  With feat == nullptr the closed-form
-// radius goes to chunk_r; otherwise feat, lvl and the cell side (in chunk_r,
-// which the network's radius pass scales in place) are written.
-int chunk_feat_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
-                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r,
-                   float *feat, uint8_t *lvl)
+// Closed-form first radius of every chunk of a batched pass.
+int chunk_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                     const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r)
 {
     int64_t blocks = (n_chunks + 7) / 8;
     blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 16);
     if (blocks < 1) blocks = 1;
-    const bool closed = feat == nullptr;
     chunk_feat_kernel<float><<<(unsigned)blocks, 256, 0, c->stream>>>(
-        (const float4 *)spos, keys, cellT, 0, 0, n_chunks, qpw, 1.f, 1.f, k, 0.25f,
-        closed ? chunk_r : nullptr, feat, lvl, nullptr, nullptr, seg, B, closed ? nullptr : chunk_r);
+        (const float4 *)spos, keys, cellT, 0, 0, n_chunks, qpw, 1.f, 1.f, k, 0.25f, chunk_r, nullptr, nullptr,
+        nullptr, nullptr, seg, B);
     HOP_LAUNCH(c);
     return HOP_OK;
 }

@@ -252,9 +252,8 @@ int chunk_features(hop_ctx *c, const void *spos, const uint64_t *keys, const uin
 int grid_build_seg(hop_ctx *c, const float *pos, int64_t n, const SegDesc *seg, int B,
                    int64_t n_cells, void **spos_out, uint32_t **perm_out, uint64_t **keys_out,
                    uint32_t **cellT_out);
-int chunk_feat_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
-                   const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r,
-                   float *feat, uint8_t *lvl);
+int chunk_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
+                     const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r);
 int mlp_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
                    const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r);
 

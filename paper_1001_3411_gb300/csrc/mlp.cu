@@ -42,11 +42,10 @@ __device__ __forceinline__ float mlp_forward_one(const float *W, const float *x,
 }
 
 // out[s] = MLP(feat[s]); with lvl != null the output is the search radius
-// side(lvl) * exp(y + margin) instead, and with side != null it is
-// side[s] * exp(y + margin) (side may alias out).
+// side(lvl) * exp(y + margin) instead.
 __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const float *__restrict__ feat,
-                               int64_t m, float *out, const uint8_t *__restrict__ lvl,
-                               double box, float margin, const float *side)
+                               int64_t m, float *__restrict__ out, const uint8_t *__restrict__ lvl,
+                               double box, float margin)
 {
     __shared__ float W[NP];
     for (int i = threadIdx.x; i < NP; i += blockDim.x) W[i] = bf(w16, i);
@@ -57,9 +56,7 @@ __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const floa
 #pragma unroll
         for (int f = 0; f < IN; ++f) x[f] = feat[s * IN + f];
         const float y = mlp_forward_one(W, x, h1);
-        if (side) {
-            out[s] = side[s] * expf(y + margin);
-        } else if (lvl) {
+        if (lvl) {
             const float sd = (float)(box / (double)(1u << lvl[s]));
             out[s] = sd * expf(y + margin);
         } else {
@@ -272,7 +269,7 @@ int mlp_forward_dev(hop_ctx *c, const float *feat, int64_t m, float *out)
     int64_t blocks = std::min<int64_t>((m + 127) / 128, (int64_t)c->num_sms * 8);
     blocks = std::max<int64_t>(blocks, 1);
     mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat, m,
-                                                           out, nullptr, 1.0, 0.f, nullptr);
+                                                           out, nullptr, 1.0, 0.f);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
@@ -308,7 +305,7 @@ int mlp_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_
     int64_t blocks = std::min<int64_t>((nc + 127) / 128, (int64_t)c->num_sms * 8);
     blocks = std::max<int64_t>(blocks, 1);
     mlp_fwd_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>((const __nv_bfloat16 *)c->mlp->w16, feat, nc,
-                                                           chunk_r, lvl, p->box, c->mlp->log_margin, nullptr);
+                                                           chunk_r, lvl, p->box, c->mlp->log_margin);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
