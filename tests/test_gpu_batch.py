@@ -204,3 +204,29 @@ def test_batch_argument_errors(hop):
     # the context still works after the errors
     r = hop.hop_run_batch(d, off, boxes, p)
     assert r["n_groups"].shape == (2,)
+
+
+def test_cached_graph_survives_scratch_moving_under_it(hop):
+    """A single-box call on a larger box grows (and so moves) the context's
+    scratch; the next batched call must notice and capture again."""
+    sizes, boxes = [3000, 777, 20011], [1.0, 0.5, 2.0]
+    pos, off = _batch(sizes, boxes, 11)
+    d = torch.from_numpy(pos).cuda()
+    hop.set_tuning(8, 1)
+    p = hopgpu.default_params(radius_mode=hopgpu.HOP_RADIUS_COUNT)
+    first = hop.hop_run_batch(d, off, boxes, p, ld_nbr=16)
+    big = torch.from_numpy(synth.nfw_box(400000, 12)[0]).cuda()
+    hop.hop_run(big, hopgpu.default_params(), ld_nbr=16)
+    again = hop.hop_run_batch(d, off, boxes, p, ld_nbr=16)
+    for k in ("dens", "group", "nbr"):
+        assert torch.equal(first[k], again[k]), k
+    # a new radius margin is part of the captured pass too
+    hop.set_tuning(8, 1)
+    w, m = radius_model.load()[8]
+    hop.hop_mlp_load(w, m + 0.05)
+    pl = hopgpu.default_params(radius_mode=hopgpu.HOP_RADIUS_LEARNED)
+    a = hop.hop_run_batch(d, off, boxes, pl, ld_nbr=16)
+    hop.hop_mlp_load(w, m)
+    b = hop.hop_run_batch(d, off, boxes, pl, ld_nbr=16)
+    for k in ("dens", "group", "nbr"):
+        assert torch.equal(a[k], first[k]) and torch.equal(b[k], first[k]), k
