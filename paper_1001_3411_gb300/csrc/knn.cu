@@ -217,13 +217,144 @@ __device__ void rows_scan(bool need, const int *grows, int gtot, int k, int n_ou
     ok = !need || (hk && bk > 0 && (n_out <= 0 || (ho && bo > 0)));
 }
 
+// Bit patterns of non-negative values, which order like the values; a
+// window bin (0 < bin) holds the values sharing the top S0-shifted bits.
+template <typename T> struct FBits;
+template <> struct FBits<float> {
+    using U = uint32_t;
+    static constexpr int S0 = 20;
+    __device__ static U of(float v) { return __float_as_uint(v); }
+    __device__ static float val(U u) { return __uint_as_float(u); }
+};
+template <> struct FBits<double> {
+    using U = unsigned long long;
+    static constexpr int S0 = 49;
+    __device__ static U of(double v) { return (U)__double_as_longlong(v); }
+    __device__ static double val(U u) { return __longlong_as_double((long long)u); }
+};
+
+// Exact k-th smallest value of each needing group's buffer when its window
+// bin bk (0 < bk; below entries under it, upto up to it) holds more than
+// KCAP entries -- a dense clump at the k-th distance.  A radix descent on
+// the bit pattern (5 bits per level, a 32-bin histogram of the bin's
+// entries sharing the prefix so far, built by the group's P lanes) narrows
+// the bin until at most KCAP entries, or a single value, remain; those are
+// gathered and ranked.  A bin below the top shares the top bits of its
+// values, so the descent starts there; the top bin also takes every value
+// above the window (when the window was moved down), so there the descent
+// starts from the full pattern.  Written to *out.
+template <typename T, int P>
+__device__ void warp_kth_deep(bool need, const T *bd, int cnt, int cmax, int *hist, int tb, int bk, int below,
+                              int upto, int k, int p, uint32_t gmask, uint32_t lt_mask, T *kd, T *out)
+{
+    using B = FBits<T>;
+    using U = typename B::U;
+    constexpr int PER = kHistBins / P;
+    constexpr int W = 8 * (int)sizeof(U);
+    const bool top = bk == kHistBins - 1;
+    U pfx = top ? U(0) : (U)(tb - (kHistBins - 1) + bk);
+    int shift = top ? W : B::S0;
+    // an entry of the sub-bin: in window bin bk and sharing the prefix
+    auto match = [&](T v) {
+        const U u = B::of(v);
+        return (shift >= W || (u >> shift) == pfx) && (!top || bin_of(v, tb) == bk);
+    };
+    bool go = need && upto - below > KCAP;
+    for (int guard = 0; guard < 16 && __any_sync(FULL, go); ++guard) {
+        const int sh = shift > 5 ? shift - 5 : 0;
+        const U dmask = (U(1) << (shift - sh)) - 1;
+        if (go)
+            for (int b = p; b < kHistBins; b += P) hist[b] = 0;
+        __syncwarp();
+        for (int e0 = 0; e0 < cmax; e0 += P) {
+            const int e = e0 + p;
+            if (go && e < cnt) {
+                const T v = bd[e];
+                if (match(v)) atomicAdd(&hist[(int)((B::of(v) >> sh) & dmask)], 1);
+            }
+        }
+        __syncwarp();
+        // the first digit whose running count reaches k: each lane sums
+        // PER digits, a prefix over the group finds the lane that holds it
+        int mine = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) mine += go ? hist[p * PER + i] : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < P; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o, P);
+            if (p >= o) incl += y;
+        }
+        const int excl = incl - mine;
+        int fd = -1, fb = 0, fu = 0;
+        if (go && below + excl < k && k <= below + incl) {
+            int cum = below + excl;
+            for (int i = 0; i < PER; ++i) {
+                const int h = hist[p * PER + i];
+                if (cum + h >= k) { fd = p * PER + i; fb = cum; fu = cum + h; break; }
+                cum += h;
+            }
+        }
+        const uint32_t hd = __ballot_sync(FULL, fd >= 0) & gmask;
+        const int ld = hd ? __ffs(hd) - 1 : 0;
+        const int gd = __shfl_sync(FULL, fd, ld), gb = __shfl_sync(FULL, fb, ld), gu = __shfl_sync(FULL, fu, ld);
+        if (go) {
+            if (hd) {
+                pfx = shift >= W ? (U)gd : ((pfx << (shift - sh)) | (U)gd);
+                below = gb;
+                upto = gu;
+                shift = sh;
+            }
+            go = hd && shift > 0 && upto - below > KCAP;
+        }
+        __syncwarp();
+    }
+    int nk = 0;
+    for (int e0 = 0; e0 < cmax; e0 += P) {
+        const int e = e0 + p;
+        T v = T(0);
+        bool in = false;
+        if (need && e < cnt) {
+            v = bd[e];
+            in = match(v);
+        }
+        const uint32_t m = __ballot_sync(FULL, in) & gmask;
+        if (in) {
+            const int pos = nk + __popc(m & lt_mask);
+            if (pos < KCAP) kd[pos] = v;
+        }
+        nk += __popc(m);
+    }
+    __syncwarp();
+    const bool small = nk <= KCAP;
+    // more than KCAP entries with the whole bit pattern in common: one value
+    if (need && !small && p == 0) *out = B::val(shift >= W ? U(0) : (pfx << shift));
+    const int nkmax = warp_max_i((need && small) ? nk : 0);
+    for (int e0 = 0; e0 < nkmax; e0 += P) {
+        const int e = e0 + p;
+        const bool mine = need && small && e < nk;
+        const T v = mine ? kd[e] : T(0);
+        int lt = below, le = below;
+        for (int f = 0; f < nkmax; ++f) {
+            if (f < nk) {
+                const T u = kd[f];
+                lt += u < v;
+                le += u <= v;
+            }
+        }
+        if (mine && lt < k && k <= le) *out = v;
+    }
+    __syncwarp();
+}
+
 // Exact k-th smallest value of each needing group's buffer, given that it
 // lies in bin bk with below_k smaller entries: the entries of bin bk are
-// gathered into a small list and ranked there (the whole buffer is scanned
-// only when the bin is crowded).  Written to *out.
+// gathered into a small list and ranked there; a crowded bin goes through
+// warp_kth_deep (the open lowest bin, values next to zero, is ranked in the
+// whole buffer).  Written to *out.
 template <typename T, int P>
-__device__ void warp_kth(bool need, const T *bd, int cnt, int cmax, int tb, int bk, int below_k,
-                         int k, int p, uint32_t gmask, uint32_t lt_mask, T *kd, T *out)
+__device__ void warp_kth(bool need, const T *bd, int cnt, int cmax, int *hist, int tb, int bk, int below_k,
+                         int upto_k, int k, int p, uint32_t gmask, uint32_t lt_mask, T *kd, T *out)
 {
     int nk = 0;
     for (int e0 = 0; e0 < cmax; e0 += P) {
@@ -258,10 +389,13 @@ __device__ void warp_kth(bool need, const T *bd, int cnt, int cmax, int tb, int 
         }
         if (mine && lt < k && k <= le) *out = v;
     }
-    if (__any_sync(FULL, need && !small)) {
+    if (__any_sync(FULL, need && !small && bk > 0))
+        warp_kth_deep<T, P>(need && !small && bk > 0, bd, cnt, cmax, hist, tb, bk, below_k, upto_k, k, p, gmask,
+                            lt_mask, kd, out);
+    if (__any_sync(FULL, need && !small && bk == 0)) {
         for (int e0 = 0; e0 < cmax; e0 += P) {
             const int e = e0 + p;
-            if (need && !small && e < cnt) {
+            if (need && !small && bk == 0 && e < cnt) {
                 const T v = bd[e];
                 if (bin_of(v, tb) == bk) {
                     int lt = below_k, le = below_k;
@@ -706,8 +840,8 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                                              ? bin_upper(tau, tb, bk) : T(-1);
                                 const bool exact = need && !(ntau >= T(0));
                                 if (__any_sync(FULL, exact)) {
-                                    warp_kth<T, P>(exact, bd, cnt, cmax, tb, bk, below_k, k, p, gmask, lt_mask,
-                                                   kd, &kthv[q]);
+                                    warp_kth<T, P>(exact, bd, cnt, cmax, hist, tb, bk, below_k, upto_k, k, p,
+                                                   gmask, lt_mask, kd, &kthv[q]);
                                     if (exact) ntau = kthv[q];
                                     __syncwarp();
                                 }
@@ -812,10 +946,14 @@ __global__ void __launch_bounds__(kKnnThreads, 4) knn_kernel(KnnDev<T> a)
                     }
                     if (mine && lt < k && k <= le) kthv[q] = v;
                 }
-                if (__any_sync(FULL, need && !small)) {
+                __syncwarp();
+                if (__any_sync(FULL, need && !small && bk > 0))
+                    warp_kth_deep<T, P>(need && !small && bk > 0, bd, cnt, cmax, hist, tb, bk, below_k, upto_k, k,
+                                        p, gmask, lt_mask, kd, &kthv[q]);
+                if (__any_sync(FULL, need && !small && bk == 0)) {
                     for (int e0 = 0; e0 < cmax; e0 += P) {
                         const int e = e0 + p;
-                        if (!(need && !small && e < cnt)) continue;
+                        if (!(need && !small && bk == 0 && e < cnt)) continue;
                         const T v = bd[e];
                         if (bin_of(v, tb) != bk) continue;
                         int lt = below_k, le = below_k;
