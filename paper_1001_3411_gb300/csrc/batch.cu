@@ -257,6 +257,14 @@ int enqueue_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const Pass
     a.seg = seg;
     a.B = pl.B;
     a.n_chunks = pl.n_chunks;
+    if (pl.B == 1) {
+        // one subvolume: the kernel without per-chunk descriptors, with the
+        // same box, table, radius and normalisation as kernel arguments
+        a.seg = nullptr;
+        a.level_dense = pl.seg[0].level_dense;
+        a.box = pl.seg[0].box;
+        a.plain_r = pl.seg[0].plain_r;
+    }
     rc = knn_launch(c, a, false, c->qpw, c->cpr);
     if (rc) return rc;
     if ((rc = record(c, 3))) return rc;
