@@ -37,6 +37,7 @@ def main(argv=None):
     ap.add_argument("--cpr", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--path", choices=["batch", "eager", "single"], default="batch")
+    ap.add_argument("--halo", action="store_true", help="also compute the halo statistics of each pass")
     a = ap.parse_args(argv)
     build_library()
     pos, _ = synth.nfw_box(a.n, synth.workload_seed(3))
@@ -50,10 +51,16 @@ def main(argv=None):
     p = default_params(radius_mode=mode)
     for i in range(a.steps):
         if a.path in ("batch", "eager"):
-            h.hop_run_batch(d, [0, a.n], [1.0], p, eager=a.path == "eager")
+            r = h.hop_run_batch(d, [0, a.n], [1.0], p, eager=a.path == "eager")
+            ng = int(r["n_groups"][0])
         else:
-            h.hop_run(d, p)
-        print(json.dumps(dict(step=i, **h.stats())), flush=True)
+            r = h.hop_run(d, p)
+            ng = r["n_groups"]
+        line = dict(step=i, **h.stats())
+        if a.halo:
+            h.hop_halo_stats(d, r["dens"], r["group"], ng)
+            line["halo_ms"] = h.stats()["ms_total"]
+        print(json.dumps(line), flush=True)
     h.close()
 
 
