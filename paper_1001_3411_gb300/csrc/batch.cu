@@ -509,8 +509,9 @@ int hop_run_batch(hop_ctx *c, const float *pos, const int64_t *offsets, const do
                                     cudaMemcpyDeviceToHost, c->stream));
         HOP_CUDA(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
         HOP_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (herr == kErrTableFull) {
-            // the boundary table overflowed: a larger one, a new capture
+        if (herr == kErrTableFull && attempt < 3) {
+            // the boundary table overflowed: a larger one, a new capture (the
+            // last attempt keeps the error word for the report below)
             HOP_CUDA(c, cudaMemsetAsync(c->d_err, 0, 4, c->stream));
             cap <<= 2;
             continue;
