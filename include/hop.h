@@ -265,17 +265,18 @@ int hop_link_static(const float *dens, const uint32_t *nbr, int32_t ld_nbr, int6
  * the merging description).  Particle masses are equal, so a halo's mass
  * is its member count.  In the periodic box the centre of mass is taken
  * about the halo's peak particle (its densest member, then the smaller
- * index): the members' minimum-image offsets from the peak are averaged in
- * fp64 and added to the peak's position, then wrapped into [0, box).  The
+ * index): the members' minimum-image offsets from the peak are averaged and
+ * added to the peak's position, then wrapped into [0, box).  The offsets
+ * are summed in fixed point (2^-32 of the box), so centres are reproducible
+ * and within 2^-33 of the box of the exact mean.  The
  * maximum radius is the largest minimum-image distance from that centre to
  * a member.  All pointers are device memory, in the caller's order:
  *   pos    n x 3 float32 (float64 if pos_is_f64), as given to hop_run;
  *   dens   n float32; group n int32 (-1 = no halo, else < n_groups);
  *   count  n_groups int64, peak n_groups uint32 (particle index),
  *   com    n_groups x 3 float64, rmax n_groups float64 (outputs).
- * A group id >= n_groups is HOP_EINVAL.  Sums are fp64 atomics, so the
- * centres may differ in the last bits between runs.  Synchronises the
- * stream; hop_get_stats reports the time in ms_total.
+ * A group id >= n_groups is HOP_EINVAL.  Synchronises the stream;
+ * hop_get_stats reports the time in ms_total.
  */
 int hop_halo_stats(hop_ctx *ctx, const void *pos, int32_t pos_is_f64, const float *dens,
                    const int32_t *group, int64_t n, int64_t n_groups, double box,

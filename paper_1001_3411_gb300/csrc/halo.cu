@@ -3,8 +3,11 @@
 // end of the merging description).  Particle masses are equal, so the mass
 // is the member count.  In the periodic box the centre of mass is taken
 // about the halo's peak particle (its densest member, then the smaller
-// index): members' minimum-image offsets from the peak are averaged (fp64)
-// and added to the peak's position, wrapped into [0, box).  The maximum
+// index): members' minimum-image offsets from the peak are averaged and
+// added to the peak's position, wrapped into [0, box).  The offsets are
+// summed in fixed point (2^-32 of the box, int64 atomics), so the centres do
+// not depend on the order of the sums and lie within 2^-33 of the box of
+// the exact mean.  The maximum
 // radius is the largest minimum-image distance from that centre to a member.
 //
 // Four grid-stride passes over the particles, each HBM-bound: peak keys and
@@ -31,9 +34,9 @@ template <typename T> __device__ __forceinline__ double coord(const T *pos, int6
 
 // Sum (or max) over the lanes of `peers` (all lanes holding the same group);
 // every lane of the set gets the result.
-__device__ __forceinline__ double peer_sum(uint32_t peers, double v)
+__device__ __forceinline__ long long peer_sum_ll(uint32_t peers, long long v)
 {
-    double s = 0.0;
+    long long s = 0;
     for (uint32_t m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
     return s;
 }
@@ -74,8 +77,10 @@ __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *
 
 template <typename T>
 __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__restrict__ group, int64_t n, int64_t G,
-                                double box, const unsigned long long *__restrict__ pkey, double *__restrict__ sum)
+                                double box, const unsigned long long *__restrict__ pkey,
+                                unsigned long long *__restrict__ sum)
 {
+    const double scale = 4294967296.0 / box;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -85,18 +90,20 @@ __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__rest
         if (g < 0) continue;
         const uint32_t peers = __match_any_sync(active, g);
         const int64_t p = (int64_t)(0xFFFFFFFFu - (uint32_t)pkey[g]);
-        double o[3];
+        long long o[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) o[d] = peer_sum(peers, min_image_d(coord(pos, i, d) - coord(pos, p, d), box));
+        for (int d = 0; d < 3; ++d)
+            o[d] = peer_sum_ll(peers, __double2ll_rn(min_image_d(coord(pos, i, d) - coord(pos, p, d), box) * scale));
         if ((threadIdx.x & 31) == __ffs(peers) - 1)
-            for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g + d], o[d]);
+            for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g + d], (unsigned long long)o[d]);
     }
 }
 
 template <typename T>
 __global__ void halo_centre_kernel(const T *__restrict__ pos, int64_t G, double box,
                                    const unsigned long long *__restrict__ pkey,
-                                   const unsigned long long *__restrict__ cnt, const double *__restrict__ sum,
+                                   const unsigned long long *__restrict__ cnt,
+                                   const unsigned long long *__restrict__ sum,
                                    int64_t *__restrict__ count, uint32_t *__restrict__ peak, double *__restrict__ com)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
@@ -107,7 +114,8 @@ __global__ void halo_centre_kernel(const T *__restrict__ pos, int64_t G, double 
         peak[g] = p;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double x = c ? coord(pos, (int64_t)p, d) + sum[3 * g + d] / (double)c : 0.0;
+            const double mean = (double)(long long)sum[3 * g + d] / (double)c * (box / 4294967296.0);
+            double x = c ? coord(pos, (int64_t)p, d) + mean : 0.0;
             if (x < 0.0) x += box;
             if (x >= box) x -= box;
             com[3 * g + d] = x;
@@ -160,8 +168,7 @@ int halo_stats_t(hop_ctx *c, const T *pos, const float *dens, const int32_t *gro
     // scratch: peak keys, counts, offset sums (3), radius bits
     char *s = (char *)ctx_buf(c, S_HALO, (size_t)G * 6 * 8);
     if (!s) return HOP_ENOMEM;
-    unsigned long long *pkey = (unsigned long long *)s, *cnt = pkey + G, *rbits = cnt + G;
-    double *sum = (double *)(rbits + G);
+    unsigned long long *pkey = (unsigned long long *)s, *cnt = pkey + G, *rbits = cnt + G, *sum = rbits + G;
     HOP_CUDA(c, cudaMemsetAsync(s, 0, (size_t)G * 6 * 8, c->stream));
     halo_peak_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dens, group, n, G, pkey, cnt, c->d_err);
     HOP_LAUNCH(c);
