@@ -8,8 +8,9 @@ particles) through ctypes; the library is compiled with gcc on first use.
 
 Functions follow HOP as restated in Parallel HOP (arXiv:1001.3411), Sec. 2:
 ``knn`` (C1), ``density`` (C2), ``link`` (C3, C4), ``boundaries`` (C5),
-``merge`` (C6, C7), ``halo_stats`` (C8, Sec. 3) and ``hop`` (C1-C7).  Every function is pinned by
-``tests/test_oracle_pins.py``.
+``merge`` (C6, C7), ``halo_stats`` (C8, Sec. 3), ``hop`` (C1-C7) and
+ADAPTAHOP's subhalos (C9, Sec. 6): ``sym_boundaries`` and ``subhalos``.
+Every function is pinned by the ``tests/test_oracle_*.py`` files.
 """
 from __future__ import annotations
 
@@ -53,9 +54,11 @@ def _L():
             lib.orc_boundaries.argtypes = [vp, vp, vp, i32, i64, i32, dbl, vp, vp, vp, i64, vp]
             lib.orc_merge.argtypes = [vp, vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp, vp]
             lib.orc_halo_stats.argtypes = [vp, vp, vp, i64, i64, dbl, vp, vp, vp, vp]
+            lib.orc_sym_boundaries.argtypes = [vp, vp, vp, i32, i64, i32, dbl, vp, vp, vp, i64, vp]
+            lib.orc_subhalos.argtypes = [vp, vp, i64, vp, vp, vp, i64, vp, i32, i64, dbl, vp, vp]
             lib.orc_set_threads.argtypes = [C.c_int]
             for f in ("orc_knn", "orc_density", "orc_link", "orc_boundaries", "orc_merge",
-                      "orc_halo_stats", "orc_num_threads"):
+                      "orc_halo_stats", "orc_sym_boundaries", "orc_subhalos", "orc_num_threads"):
                 getattr(lib, f).restype = C.c_int
             _lib = lib
     return _lib
@@ -112,26 +115,58 @@ def link(dens, nbr, n_hop: int):
     return hop, chain
 
 
-def boundaries(chain, dens, nbr, n_merge: int, delta_outer: float):
-    """C5: (lo int32 [E], hi int32 [E], s float64 [E]) ordered by (lo, hi);
-    s is the maximum summed density (twice the average) per chain pair."""
+def _table(fn, what, chain, dens, nbr, n_merge, delta_outer):
     chain = np.ascontiguousarray(chain, dtype=np.int32)
     dens = np.ascontiguousarray(dens, dtype=np.float64)
     nbr = np.ascontiguousarray(nbr, dtype=np.int32)
     n, ld = nbr.shape
     ne = C.c_int64(0)
-    L = _L()
-    rc = L.orc_boundaries(_p(chain), _p(dens), _p(nbr), ld, n, int(n_merge), float(delta_outer),
-                          None, None, None, 0, C.byref(ne))
-    _check(rc, "boundaries")
+    _check(fn(_p(chain), _p(dens), _p(nbr), ld, n, int(n_merge), float(delta_outer),
+              None, None, None, 0, C.byref(ne)), what)
     cap = max(1, ne.value)
     lo = np.empty(cap, dtype=np.int32)
     hi = np.empty(cap, dtype=np.int32)
     s = np.empty(cap, dtype=np.float64)
-    _check(L.orc_boundaries(_p(chain), _p(dens), _p(nbr), ld, n, int(n_merge), float(delta_outer),
-                            _p(lo), _p(hi), _p(s), cap, C.byref(ne)), "boundaries")
+    _check(fn(_p(chain), _p(dens), _p(nbr), ld, n, int(n_merge), float(delta_outer),
+              _p(lo), _p(hi), _p(s), cap, C.byref(ne)), what)
     e = ne.value
     return lo[:e], hi[:e], s[:e]
+
+
+def boundaries(chain, dens, nbr, n_merge: int, delta_outer: float):
+    """C5: (lo int32 [E], hi int32 [E], s float64 [E]) ordered by (lo, hi);
+    s is the maximum summed density (twice the average) per chain pair."""
+    return _table(_L().orc_boundaries, "boundaries", chain, dens, nbr, n_merge, delta_outer)
+
+
+def sym_boundaries(chain, dens, nbr, n_merge: int, delta_outer: float):
+    """C9a: the pairs of C5 whose chains link each other in both directions
+    (lo, hi, s as in ``boundaries``)."""
+    return _table(_L().orc_sym_boundaries, "sym_boundaries", chain, dens, nbr, n_merge, delta_outer)
+
+
+def subhalos(chain, dens, lo, hi, s, levels, n_min: int = 1, f_poisson: float = 0.0):
+    """C9b: (sub int32 [L, n], n_sub int64 [L]) for the thresholds in
+    ``levels``: per level, the rank of each particle's subhalo or -1."""
+    chain = np.ascontiguousarray(chain, dtype=np.int32)
+    dens = np.ascontiguousarray(dens, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.int32)
+    hi = np.ascontiguousarray(hi, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    lv = np.ascontiguousarray(np.atleast_1d(levels), dtype=np.float64)
+    n = chain.shape[0]
+    sub = np.empty((len(lv), n), dtype=np.int32)
+    n_sub = np.zeros(len(lv), dtype=np.int64)
+    _check(_L().orc_subhalos(_p(chain), _p(dens), n, _p(lo), _p(hi), _p(s), lo.shape[0], _p(lv),
+                             len(lv), int(n_min), float(f_poisson), _p(sub), _p(n_sub)), "subhalos")
+    return sub, n_sub
+
+
+def adaptahop(chain, dens, nbr, n_merge: int, delta_outer: float, levels, n_min: int = 1,
+              f_poisson: float = 0.0):
+    """C9: symmetric boundaries, then subhalos at every level."""
+    lo, hi, s = sym_boundaries(chain, dens, nbr, n_merge, delta_outer)
+    return subhalos(chain, dens, lo, hi, s, levels, n_min, f_poisson)
 
 
 def merge(chain, dens, lo, hi, s, delta_outer: float, delta_saddle: float, delta_peak: float):

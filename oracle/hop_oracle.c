@@ -28,6 +28,9 @@
  *                  groups are numbered by (peak density desc, peak index asc).
  *   C8 halo stats  mass, centre of mass and maximum radius of every halo
  *                  (Sec. 3, last paragraph of the merging description).
+ *   C9 subhalos    ADAPTAHOP's extension (Sec. 6): symmetric boundaries
+ *                  only, links below a threshold delta_s destroyed, one
+ *                  labelling per delta_s, Poisson significance cut.
  *
  * Arithmetic: positions are taken as doubles (fp32 inputs promote exactly);
  * distances, kernel sums and boundary sums are fp64.  Densities handed in
@@ -464,4 +467,159 @@ int orc_halo_stats(const double *pos, const double *dens, const int32_t *group, 
     }
     free(sum);
     return ORC_OK;
+}
+
+/* Directed link a -> b with its summed density; ordered by (a, b, s desc). */
+typedef struct { int32_t a, b; double s; } orc_dlink_t;
+
+static int dlink_cmp(const void *pa, const void *pb)
+{
+    const orc_dlink_t *x = (const orc_dlink_t *)pa, *y = (const orc_dlink_t *)pb;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    if (x->s != y->s) return x->s > y->s ? -1 : 1;
+    return 0;
+}
+
+/*
+ * C9a.  ADAPTAHOP's symmetric boundaries (Sec. 6, subhalos).  A directed
+ * link a -> b exists when some particle i of chain a with dens_i >= d_outer
+ * has, among the first n_merge entries of its list, a j != i of chain
+ * b != a with dens_j >= d_outer (the particle filter of C5).  A pair {a, b}
+ * is a symmetric boundary only when both a -> b and b -> a exist; its value
+ * s is the largest dens_i + dens_j over the links of both directions (the
+ * value C5 gives the same pair).  Output as in C5: one entry per kept pair,
+ * ordered by (lo, hi); *n_out is always set; with lo/hi/s NULL the call
+ * only reports it, and with cap too small it returns ORC_ECAP.
+ */
+int orc_sym_boundaries(const int32_t *chain, const double *dens, const int32_t *nbr,
+                       int32_t ld, int64_t n, int32_t n_merge, double d_outer,
+                       int32_t *lo, int32_t *hi, double *s, int64_t cap, int64_t *n_out)
+{
+    if (!chain || !dens || !nbr || !n_out || n_merge <= 0 || ld < n_merge) return ORC_EINVAL;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(dens[i] >= d_outer)) continue;
+        for (int32_t t = 0; t < n_merge; ++t) {
+            const int32_t j = nbr[i * (int64_t)ld + t];
+            if (j < 0 || j >= n) return ORC_EINVAL;
+            if (j == i || !(dens[j] >= d_outer) || chain[i] == chain[j]) continue;
+            ++m;
+        }
+    }
+    orc_dlink_t *raw = (orc_dlink_t *)malloc(sizeof(orc_dlink_t) * (size_t)(m ? m : 1));
+    if (!raw) return ORC_ENOMEM;
+    int64_t w = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(dens[i] >= d_outer)) continue;
+        for (int32_t t = 0; t < n_merge; ++t) {
+            const int32_t j = nbr[i * (int64_t)ld + t];
+            if (j == i || !(dens[j] >= d_outer) || chain[i] == chain[j]) continue;
+            raw[w].a = chain[i];
+            raw[w].b = chain[j];
+            raw[w].s = dens[i] + dens[j];
+            ++w;
+        }
+    }
+    qsort(raw, (size_t)w, sizeof(orc_dlink_t), dlink_cmp);
+    /* keep the first (largest s) entry of every directed pair */
+    int64_t d = 0;
+    for (int64_t t = 0; t < w; ++t)
+        if (t == 0 || raw[t].a != raw[t - 1].a || raw[t].b != raw[t - 1].b) raw[d++] = raw[t];
+    /* a -> b with a < b is kept when b -> a exists (binary search) */
+    int64_t u = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            *n_out = u;
+            if (!lo || !hi || !s) break;
+            if (u > cap) { free(raw); return ORC_ECAP; }
+            u = 0;
+        }
+        for (int64_t t = 0; t < d; ++t) {
+            if (raw[t].a > raw[t].b) continue;
+            int64_t l = 0, r = d;
+            while (l < r) {
+                const int64_t mid = l + (r - l) / 2;
+                if (raw[mid].a < raw[t].b || (raw[mid].a == raw[t].b && raw[mid].b < raw[t].a)) l = mid + 1;
+                else r = mid;
+            }
+            if (l == d || raw[l].a != raw[t].b || raw[l].b != raw[t].a) continue;
+            if (pass == 1) {
+                lo[u] = raw[t].a;
+                hi[u] = raw[t].b;
+                s[u] = raw[t].s > raw[l].s ? raw[t].s : raw[l].s;
+            }
+            ++u;
+        }
+    }
+    free(raw);
+    return ORC_OK;
+}
+
+/*
+ * C9b.  Subhalos at each threshold delta_s = levels[l] (Sec. 6): every
+ * boundary with s < 2 delta_s (a link density below delta_s) is destroyed
+ * and chains joined by the remaining boundaries merge, transitively (the
+ * connected components of the chain graph).  A particle belongs to its
+ * component's subhalo when dens_i >= delta_s.  A component with N >= 1 such
+ * members is rejected when N < n_min or when their mean density (fp64 sum
+ * in index order, divided by N) is below delta_s * (1 + f_poisson / sqrt(N)),
+ * the relative Poisson noise of a count of N scaled by f_poisson.  Accepted
+ * subhalos of a level are numbered by their peak member (density desc,
+ * index asc).  sub[l * n + i] = that number, or -1; n_sub[l] = the number
+ * accepted.  Boundary ends are chain labels in [0, n).
+ */
+int orc_subhalos(const int32_t *chain, const double *dens, int64_t n,
+                 const int32_t *lo, const int32_t *hi, const double *s, int64_t ne,
+                 const double *levels, int32_t n_levels, int64_t n_min, double f_poisson,
+                 int32_t *sub, int64_t *n_sub)
+{
+    if (!chain || !dens || !levels || !sub || !n_sub || n <= 0 || n_levels <= 0 || n_min < 1 ||
+        !(f_poisson >= 0.0))
+        return ORC_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (chain[i] < 0 || chain[i] >= n) return ORC_EINVAL;
+    for (int64_t e = 0; e < ne; ++e)
+        if (lo[e] < 0 || lo[e] >= n || hi[e] < 0 || hi[e] >= n) return ORC_EINVAL;
+    int rc = ORC_ENOMEM;
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *sum = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *peak = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    orc_peak_t *pk = (orc_peak_t *)malloc(sizeof(orc_peak_t) * (size_t)n);
+    if (!parent || !cnt || !sum || !peak || !rank || !pk) goto done;
+    for (int32_t l = 0; l < n_levels; ++l) {
+        const double ds = levels[l];
+        for (int64_t c = 0; c < n; ++c) { parent[c] = (int32_t)c; cnt[c] = 0; sum[c] = 0.0; peak[c] = -1; rank[c] = -1; }
+        for (int64_t e = 0; e < ne; ++e) {
+            if (!(s[e] >= 2.0 * ds)) continue;
+            const int32_t a = uf_find(parent, lo[e]), b = uf_find(parent, hi[e]);
+            if (a != b) parent[a] = b;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(dens[i] >= ds)) continue;
+            const int32_t r = uf_find(parent, chain[i]);
+            ++cnt[r];
+            sum[r] += dens[i];
+            if (peak[r] < 0 || key_greater(dens, (int32_t)i, peak[r])) peak[r] = (int32_t)i;
+        }
+        int64_t g = 0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (cnt[c] == 0 || cnt[c] < n_min) continue;
+            const double N = (double)cnt[c];
+            if (!(sum[c] / N >= ds * (1.0 + f_poisson / sqrt(N)))) continue;
+            pk[g].d = dens[peak[c]]; pk[g].idx = peak[c]; pk[g].set = (int32_t)c; ++g;
+        }
+        qsort(pk, (size_t)g, sizeof(orc_peak_t), peak_cmp);
+        for (int64_t t = 0; t < g; ++t) rank[pk[t].set] = (int32_t)t;
+        int32_t *out = sub + (int64_t)l * n;
+        for (int64_t i = 0; i < n; ++i)
+            out[i] = dens[i] >= ds ? rank[uf_find(parent, chain[i])] : -1;
+        n_sub[l] = g;
+    }
+    rc = ORC_OK;
+done:
+    free(parent); free(cnt); free(sum); free(peak); free(rank); free(pk);
+    return rc;
 }

@@ -161,6 +161,29 @@ def plummer_box(n_spheres: int = 20, n_per: int = 1146, a: float = 0.01,
     return pos, cen
 
 
+def plummer_pair(n_per: int = 1500, a: float = 0.01, sep: float = 0.04, n_background: int = 3000,
+                 seed: int = 0, box: float = 1.0, r_max: float = 0.25, dtype=np.float64) -> np.ndarray:
+    """Two Plummer spheres of n_per particles (scale radius a) whose centres
+    sit sep apart along x about the box centre, plus a uniform background: a
+    halo with one subhalo.  Returns (pos, centres)."""
+    cen = np.array([[0.5 * box - 0.5 * sep, 0.5 * box, 0.5 * box],
+                    [0.5 * box + 0.5 * sep, 0.5 * box, 0.5 * box]])
+    nh = 2 * n_per
+    f_max = r_max ** 3 / (r_max ** 2 + a * a) ** 1.5
+    u = (1.0 - uniform01(seed, 40, 0, nh)) * f_max
+    r = a / np.sqrt(np.maximum(u ** (-2.0 / 3.0) - 1.0, 1e-300))
+    ex, ey, ez = _isotropic(seed, 41, 42, 0, nh)
+    hid = np.repeat(np.arange(2), n_per)
+    pos = np.empty((nh + n_background, 3), dtype=np.float64)
+    pos[:nh, 0] = cen[hid, 0] + r * ex
+    pos[:nh, 1] = cen[hid, 1] + r * ey
+    pos[:nh, 2] = cen[hid, 2] + r * ez
+    for ax in range(3):
+        pos[nh:, ax] = uniform01(seed, 50 + ax, 0, n_background) * box
+    pos = _wrap_f64(pos, box) if dtype == np.float64 else _wrap_f32(pos, box)
+    return pos, cen
+
+
 def _nfw_mu(x):
     return np.log1p(x) - x / (1.0 + x)
 
