@@ -9,7 +9,9 @@ learned first search radius; the plain-radius path is timed beside it and
 must give identical output.  Inputs are resident in HBM for `value`; `e2e`
 passes host (pinned) buffers through the same C-ABI call, copies included.
 The `batch` object times the 64-subvolume workload (graph pass, the same
-pass enqueued kernel by kernel, and one hop_run per subvolume).
+pass enqueued kernel by kernel, and one hop_run per subvolume); the
+`halo_stats` and `subhalos` objects time the halo statistics and the
+ADAPTAHOP subhalo call (five thresholds) on the learned run's output.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -49,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-subvolume section")
+    ap.add_argument("--no-subhalos", action="store_true", help="skip the ADAPTAHOP subhalo section")
     return ap.parse_args()
 
 
@@ -409,6 +412,34 @@ def run_gb300(args):
                              "basis": "12 B per particle (group id, 3 passes) + 28 B per member "
                                       "(density, position twice); peak = measured copy bandwidth"}}
 
+    # ADAPTAHOP subhalos (symmetric boundaries, one labelling per threshold)
+    # on the learned run's chains and lists: timed alone
+    sub = None
+    if not args.no_subhalos:
+        r = hop.hop_run(dpos, params["learned"], ld_nbr=N_HOP, want_chain=True)
+        levels = [80.0, 160.0, 320.0, 640.0, 1280.0]
+        subs, n_sub = hop.hop_subhalos(r["chain"], r["dens"], r["nbr"], 4, 80.0, levels)
+        del subs
+        sms, _ = timed(lambda: hop.hop_subhalos(r["chain"], r["dens"], r["nbr"], 4, 80.0, levels), args.steps,
+                       dist, hop)
+        sms /= args.steps
+        st = hop.stats()
+        ms_lv = st["ms_merge"] / len(levels)
+        # per level: key + chain id per particle in the member pass and the
+        # labelling pass, plus the label write
+        lbytes = 28 * n
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        sub = {"ms": sms, "levels": levels, "n_sub": [int(x) for x in n_sub],
+               "ms_boundaries": st["ms_boundaries"], "ms_per_level": ms_lv,
+               "symmetric_boundaries": st["n_edges"], "chains": st["n_chains"],
+               "roofline_level": {"bound": "hbm", "achieved": lbytes / (ms_lv * 1e-3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": lbytes / (ms_lv * 1e-3) / 1e9 / hbm, "traffic": None,
+                                  "basis": "28 B per particle per level (density key and chain id read twice, "
+                                           "label written); the level time includes its host-driven "
+                                           "component rounds"}}
+        del r
+        torch.cuda.empty_cache()
+
     # the single-volume call (hop_run, host round trips between stages) on
     # the same box and tuning, for comparison
     configure("learned")
@@ -501,6 +532,7 @@ def run_gb300(args):
                 "h2d_bytes_per_step": n * 12, "d2h_bytes_per_step": n * 8},
         "batch": batch,
         "halo_stats": halo,
+        "subhalos": sub,
     }
     if rank == 0:
         line["cpu_baseline"] = oracle_rate(pos, args.cpu_seconds)

@@ -282,6 +282,42 @@ int hop_halo_stats(hop_ctx *ctx, const void *pos, int32_t pos_is_f64, const floa
                    const int32_t *group, int64_t n, int64_t n_groups, double box,
                    int64_t *count, uint32_t *peak, double *com, double *rmax);
 
+/*
+ * ADAPTAHOP subhalos (Parallel HOP Sec. 6, "Parallel HOP and Subhalos"),
+ * from HOP's own densities, neighbour lists and chains:
+ *   1. symmetric boundaries: chains a and b share a boundary only when a
+ *      particle of a has a particle of b among the first n_merge entries of
+ *      its row AND a particle of b has one of a there (both particles >=
+ *      delta_outer, as in hop_boundaries).  Its value s is the largest
+ *      (double)dens_i + (double)dens_j over the links of both directions;
+ *   2. for every threshold delta_s = levels[l]: boundaries with
+ *      s < 2 delta_s are destroyed, and chains joined by the rest merge,
+ *      transitively.  A particle with dens_i >= delta_s belongs to its
+ *      merged set's subhalo;
+ *   3. a subhalo of N members is rejected when N < n_min, or when its
+ *      members' mean density (fp64 sum / N) is below
+ *      delta_s * (1 + f_poisson / sqrt(N)): the Poisson noise of a count
+ *      of N, scaled by f_poisson (0 keeps every subhalo);
+ *   4. the accepted subhalos of a level are ranked by their peak member
+ *      (density desc, index asc).
+ *   chain, dens, nbr, ld_nbr, n, n_merge, delta_outer  as in hop_boundaries
+ *            (device memory, caller's order; chain labels are roots);
+ *   levels   n_levels float32, HOST memory, each finite and >= delta_outer,
+ *            in any order;
+ *   sub      n_levels x n int32, device: sub[l * n + i] = the rank of i's
+ *            subhalo at levels[l], or -1;
+ *   n_sub    n_levels int64, host: subhalos per level.
+ * Under one threshold below another, every subhalo of the higher one lies
+ * within a single merged set of the lower (a hierarchy).  Runs the levels
+ * one after another.  Synchronises the stream.  hop_get_stats reports
+ * ms_total, ms_boundaries (step 1), ms_merge (the rest: chain ids and the
+ * levels), n_chains (chains above delta_outer) and n_edges (symmetric
+ * boundaries).
+ */
+int hop_subhalos(hop_ctx *ctx, const uint32_t *chain, const float *dens, const uint32_t *nbr,
+                 int32_t ld_nbr, int64_t n, int32_t n_merge, float delta_outer, const float *levels,
+                 int32_t n_levels, int64_t n_min, double f_poisson, int32_t *sub, int64_t *n_sub);
+
 /* Counters and stage times (ms, CUDA events on the context stream) of the
  * last hop_run / hop_density call. */
 typedef struct hop_stats {

@@ -30,7 +30,7 @@ EXPORTS = ["hop_default_params", "hop_create", "hop_destroy", "hop_set_stream", 
            "hop_set_tuning", "hop_density", "hop_link", "hop_boundaries", "hop_merge", "hop_run",
            "hop_get_stats", "hop_mlp_load", "hop_mlp_get", "hop_mlp_samples", "hop_mlp_forward",
            "hop_mlp_grad", "hop_mlp_train", "hop_link_static", "hop_run_batch", "hop_get_tuning",
-           "hop_apply_tuning", "hop_autotune", "hop_halo_stats"]
+           "hop_apply_tuning", "hop_autotune", "hop_halo_stats", "hop_subhalos"]
 
 
 class HopParams(C.Structure):
@@ -104,6 +104,7 @@ def load_library(path: str = LIB):
             "hop_run_batch": (C.c_int, [vp, vp, vp, vp, i32, P, vp, vp, vp, vp, i32, i32]),
             "hop_get_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
             "hop_halo_stats": (C.c_int, [vp, vp, i32, vp, vp, i64, i64, f64, vp, vp, vp, vp]),
+            "hop_subhalos": (C.c_int, [vp, vp, vp, vp, i32, i64, i32, f32, vp, i32, i64, f64, vp, vp]),
             "hop_apply_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
             "hop_autotune": (C.c_int, [vp, vp, vp, vp, i32, P, C.POINTER(HopTuning), i32, i32,
                                        C.POINTER(i32)]),
@@ -324,6 +325,24 @@ class Hop:
         self._check(self.L.hop_halo_stats(self.h, _ptr(pos), 1 if f64 else 0, _ptr(dens), _ptr(group), n, G,
                                           float(box), _ptr(count), _ptr(peak), _ptr(com), _ptr(rmax)))
         return count[:G], peak[:G], com[:G], rmax[:G]
+
+    def hop_subhalos(self, chain, dens, nbr, n_merge: int, delta_outer: float, levels, n_min: int = 1,
+                     f_poisson: float = 0.0):
+        """ADAPTAHOP subhalos: (sub int32 [L, n] CUDA tensor, n_sub int64
+        numpy [L]) for the thresholds in ``levels``."""
+        import torch
+        self._sync_stream()
+        n, ld = nbr.shape
+        _need(chain, torch.int32, (n,), "chain")
+        _need(dens, torch.float32, (n,), "dens")
+        _need(nbr, torch.int32, None, "nbr")
+        lv = np.ascontiguousarray(np.atleast_1d(levels), dtype=np.float32)
+        sub = torch.empty((len(lv), n), dtype=torch.int32, device=dens.device)
+        n_sub = np.zeros(len(lv), dtype=np.int64)
+        self._check(self.L.hop_subhalos(self.h, _ptr(chain), _ptr(dens), _ptr(nbr), ld, n, int(n_merge),
+                                        float(delta_outer), _ptr(lv), len(lv), int(n_min), float(f_poisson),
+                                        _ptr(sub), _ptr(n_sub)))
+        return sub, n_sub
 
     def get_tuning(self) -> dict:
         t = HopTuning()

@@ -32,24 +32,6 @@ template <typename T> __device__ __forceinline__ double coord(const T *pos, int6
     return (double)pos[3 * i + d];
 }
 
-// Sum (or max) over the lanes of `peers` (all lanes holding the same group);
-// every lane of the set gets the result.
-__device__ __forceinline__ long long peer_sum_ll(uint32_t peers, long long v)
-{
-    long long s = 0;
-    for (uint32_t m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
-    return s;
-}
-__device__ __forceinline__ unsigned long long peer_max(uint32_t peers, unsigned long long v)
-{
-    unsigned long long b = 0;
-    for (uint32_t m = peers; m; m &= m - 1) {
-        const unsigned long long u = __shfl_sync(peers, v, __ffs(m) - 1);
-        b = u > b ? u : b;
-    }
-    return b;
-}
-
 __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *__restrict__ group, int64_t n,
                                  int64_t G, unsigned long long *__restrict__ pkey,
                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ err)

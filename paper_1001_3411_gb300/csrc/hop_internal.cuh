@@ -56,6 +56,8 @@ enum Slot {
     S_SEG,                              // subvolume descriptors of a batched pass
     S_BATCH,                            // per-pass arrays of a batched pass
     S_HALO,                             // halo statistics scratch
+    S_SUB,                              // subhalos: dense chain ids, per-particle chain ids
+    S_SUB_C,                            // subhalos: arrays over chains and boundaries
     S_COUNT
 };
 
@@ -211,6 +213,31 @@ __device__ __forceinline__ int seg_of_index(const SegDesc *__restrict__ seg, int
     return lo;
 }
 
+// Warp aggregation for per-group atomics: `peers` is the set of lanes that
+// hold the same group (__match_any_sync); every lane of the set gets the
+// sum or maximum of the set's values, combined in ascending lane order.
+__device__ __forceinline__ long long peer_sum_ll(uint32_t peers, long long v)
+{
+    long long s = 0;
+    for (uint32_t m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
+    return s;
+}
+__device__ __forceinline__ double peer_sum_f64(uint32_t peers, double v)
+{
+    double s = 0.0;
+    for (uint32_t m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
+    return s;
+}
+__device__ __forceinline__ unsigned long long peer_max(uint32_t peers, unsigned long long v)
+{
+    unsigned long long b = 0;
+    for (uint32_t m = peers; m; m &= m - 1) {
+        const unsigned long long u = __shfl_sync(peers, v, __ffs(m) - 1);
+        b = u > b ? u : b;
+    }
+    return b;
+}
+
 // A size known only on the device (an edge or chain count): kernels read
 // *dev when it is set, so a captured graph needs no host round trip; `max`
 // bounds it and sizes the grid.
@@ -284,9 +311,11 @@ int knn32_launch(hop_ctx *c, const KnnArgs &a, int cpr);   // knn32.cu: one quer
 int make_dkey(hop_ctx *c, const float *dens, const uint32_t *orig, int64_t n, uint64_t *dkey);
 int hop_links(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n, int n_hop,
               uint32_t *hop, uint32_t *chain);
+// symmetric: only pairs whose chains link each other in both directions
+// (ADAPTAHOP), each with the larger of the two directions' sums.
 int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr,
                      int ld, int64_t n, int n_merge, float delta_outer,
-                     uint64_t **edge_key, double **edge_sum, int64_t *n_edges);
+                     uint64_t **edge_key, double **edge_sum, int64_t *n_edges, bool symmetric = false);
 int hop_links_async(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
                     int n_hop, uint32_t *hop, uint32_t *chain);
 int boundaries_table_async(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey,

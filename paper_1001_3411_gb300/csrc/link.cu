@@ -140,15 +140,30 @@ __device__ __forceinline__ bool table_insert(uint64_t *hkey, unsigned long long 
     return false;
 }
 
+// Slot of `key`, or -1.  Inserts never probe further than kMaxProbe.
+__device__ __forceinline__ int64_t table_find(const uint64_t *hkey, uint64_t mask, uint64_t key)
+{
+    uint64_t h = mix64(key) & mask;
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        const uint64_t k = hkey[h];
+        if (k == key) return (int64_t)h;
+        if (k == kEmpty) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
 // Boundary densities: for i with dens_i >= d_o and j among the first n_merge
 // entries of row i (j != i, dens_j >= d_o, chain_i != chain_j), the pair of
 // chain labels keeps max(dens_i + dens_j) in fp64 (exact for two fp32).  The
 // double is >= 0, so its bits order like its value and atomicMax applies.
+// With `directed` the key is (chain_i, chain_j) in that order, so the table
+// holds each direction of a pair separately (ADAPTAHOP's symmetric test).
 __global__ void boundary_kernel(const uint32_t *__restrict__ chain,
                                 const uint64_t *__restrict__ dkey,
                                 const uint32_t *__restrict__ nbr, int ld, int64_t n, int n_merge,
                                 float d_o, uint64_t *hkey, unsigned long long *hval, uint64_t mask,
-                                uint32_t *err, unsigned long long *n_ins)
+                                uint32_t *err, unsigned long long *n_ins, bool directed = false)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -164,7 +179,8 @@ __global__ void boundary_kernel(const uint32_t *__restrict__ chain,
             if (!(dj >= d_o)) continue;
             const uint32_t cj = chain[j];
             if (cj == ci) continue;
-            const uint64_t key = ci < cj ? (((uint64_t)ci << 32) | cj) : (((uint64_t)cj << 32) | ci);
+            const uint64_t key = (directed || ci < cj) ? (((uint64_t)ci << 32) | cj)
+                                                       : (((uint64_t)cj << 32) | ci);
             const double s = (double)di + (double)dj;
             if (!table_insert(hkey, hval, mask, key, (unsigned long long)__double_as_longlong(s), n_ins))
                 atomicOr(err, kErrTableFull);
@@ -191,6 +207,45 @@ __global__ void compact_table_kernel(const uint64_t *__restrict__ hkey,
         const uint32_t p = pos[h];
         ekey[p] = k;
         esum[p] = __longlong_as_double((long long)hval[h]);
+    }
+}
+
+// Symmetric boundaries (ADAPTAHOP, Parallel HOP Sec. 6) from the directed
+// table: slot (a, b) with a < b is kept when (b, a) is present too, and
+// takes the larger of the two directions' sums.  Only a < b slots are
+// written and only a > b slots are read as partners, so there is no race.
+__device__ __forceinline__ bool sym_partner(const uint64_t *hkey, uint64_t mask, uint64_t k, int64_t *r)
+{
+    if (k == kEmpty) return false;
+    const uint32_t a = (uint32_t)(k >> 32), b = (uint32_t)k;
+    if (a >= b) return false;
+    *r = table_find(hkey, mask, ((uint64_t)b << 32) | a);
+    return *r >= 0;
+}
+
+__global__ void symmetric_flag_kernel(const uint64_t *__restrict__ hkey, unsigned long long *hval, int64_t cap,
+                                      uint32_t *__restrict__ flag)
+{
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < cap;
+         h += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r;
+        const bool keep = sym_partner(hkey, (uint64_t)cap - 1, hkey[h], &r);
+        if (keep && hval[r] > hval[h]) hval[h] = hval[r];
+        flag[h] = keep ? 1u : 0u;
+    }
+}
+
+__global__ void symmetric_compact_kernel(const uint64_t *__restrict__ hkey,
+                                         const unsigned long long *__restrict__ hval, int64_t cap,
+                                         const uint32_t *__restrict__ pos, uint64_t *__restrict__ ekey,
+                                         double *__restrict__ esum)
+{
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < cap;
+         h += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r;
+        if (!sym_partner(hkey, (uint64_t)cap - 1, hkey[h], &r)) continue;
+        ekey[pos[h]] = hkey[h];
+        esum[pos[h]] = __longlong_as_double((long long)hval[h]);
     }
 }
 
@@ -275,7 +330,7 @@ int hop_links(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int
 
 int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr,
                      int ld, int64_t n, int n_merge, float delta_outer, uint64_t **edge_key,
-                     double **edge_sum, int64_t *n_edges)
+                     double **edge_sum, int64_t *n_edges, bool symmetric)
 {
     int64_t cap = 1 << 12;
     while (cap < n / 4 && cap < (int64_t(1) << 31)) cap <<= 1;
@@ -293,7 +348,7 @@ int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, co
         uint32_t *terr = (uint32_t *)(nins + 1);   // this pass's own error word
         boundary_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, nbr, ld, n, n_merge,
                                                               delta_outer, hkey, hval,
-                                                              (uint64_t)cap - 1, terr, nins);
+                                                              (uint64_t)cap - 1, terr, nins, symmetric);
         HOP_LAUNCH(c);
         HOP_CUDA(c, cudaMemcpyAsync(hn, nins, 16, cudaMemcpyDeviceToHost, c->stream));
         HOP_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -308,6 +363,21 @@ int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, co
         uint64_t *ek = (uint64_t *)ctx_buf(c, S_EDGE_KEY, std::max<int64_t>(m, 1) * sizeof(uint64_t));
         double *es = (double *)ctx_buf(c, S_EDGE_SUM, std::max<int64_t>(m, 1) * sizeof(double));
         if (!occ || !ek || !es) return HOP_ENOMEM;
+        if (symmetric) {
+            uint32_t *total = terr + 1;
+            symmetric_flag_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, hval, cap, occ);
+            HOP_LAUNCH(c);
+            int rc = scan_exclusive_u32(c, occ, occ, cap, total);
+            if (rc) return rc;
+            symmetric_compact_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, hval, cap, occ, ek, es);
+            HOP_LAUNCH(c);
+            HOP_CUDA(c, cudaMemcpyAsync(hn, nins, 16, cudaMemcpyDeviceToHost, c->stream));
+            HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+            *edge_key = ek;
+            *edge_sum = es;
+            *n_edges = *(uint32_t *)((char *)hn + 12);
+            return HOP_OK;
+        }
         occupied_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, cap, occ);
         HOP_LAUNCH(c);
         int rc = scan_exclusive_u32(c, occ, occ, cap, nullptr);

@@ -1,0 +1,363 @@
+// ADAPTAHOP subhalos on HOP's chains (Parallel HOP Sec. 6, "Parallel HOP
+// and Subhalos").
+//
+//  S1  symmetric boundary table: the directed chain-pair table (both
+//      particles >= delta_outer, as in HOP's table), kept only for pairs
+//      linked in both directions, each with the larger direction's sum
+//      (link.cu, boundaries_table with symmetric = true);
+//  S2  dense ids for the chain roots above delta_outer (scan) and, per
+//      particle above delta_outer, its root's id;
+//  then once per threshold delta_s (the paper's linear cost in the number
+//  of thresholds):
+//  S3  links with s < 2 delta_s are destroyed; the rest join chains into
+//      connected components (hook the larger root under the smaller with
+//      atomicMin, compress, repeat until no edge joins two roots);
+//  S4  members (dens >= delta_s) give each component its count, fp64
+//      density sum and peak key (warp-aggregated atomics);
+//  S5  a component is a subhalo when count >= n_min and mean density >=
+//      delta_s (1 + f_poisson / sqrt(count)); subhalos are ranked by peak
+//      key (radix sort) and every particle gets its rank or -1.
+//
+// Every per-particle pass reads a few bytes per particle plus one or two
+// gathers into the chain arrays, so the levels are HBM- and latency-bound.
+#include "hop_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kMaxRounds = 64;
+
+__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x)
+{
+    for (int g = 0; g < (1 << 24); ++g) {
+        const uint32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
+// S2: roots above delta_outer; chain labels must be roots of [0, n).
+__global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+                                 int64_t n, float d_o, uint32_t *__restrict__ flag, uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = chain[i];
+        if (c >= (uint64_t)n || chain[c] != c) atomicOr(err, kErrBadIndex);
+        flag[i] = (c == (uint32_t)i && key_dens(dkey[i]) >= d_o) ? 1u : 0u;
+    }
+}
+
+// Per particle above delta_outer: its root's dense id.  A particle above
+// delta_outer has a root above it (hops go uphill); anything else is an
+// inconsistent input.
+__global__ void particle_chain_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+                                      int64_t n, float d_o, const uint32_t *__restrict__ cid,
+                                      uint32_t *__restrict__ pc, uint32_t *__restrict__ err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = kNone;
+        if (key_dens(dkey[i]) >= d_o) {
+            const uint32_t r = chain[i];
+            if (r >= (uint64_t)n || !(key_dens(dkey[r]) >= d_o)) atomicOr(err, kErrBadIndex);
+            else v = cid[r];
+        }
+        pc[i] = v;
+    }
+}
+
+__global__ void edge_ids_kernel(const uint64_t *__restrict__ ekey, int64_t m, int64_t n,
+                                const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey, float d_o,
+                                const uint32_t *__restrict__ cid, uint32_t *__restrict__ ea,
+                                uint32_t *__restrict__ eb, uint32_t *__restrict__ err)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t lo = (uint32_t)(ekey[e] >> 32), hi = (uint32_t)ekey[e];
+        if (lo >= (uint64_t)n || hi >= (uint64_t)n || chain[lo] != lo || chain[hi] != hi ||
+            !(key_dens(dkey[lo]) >= d_o) || !(key_dens(dkey[hi]) >= d_o)) {
+            atomicOr(err, kErrBadIndex);
+            ea[e] = eb[e] = 0;
+            continue;
+        }
+        ea[e] = cid[lo];
+        eb[e] = cid[hi];
+    }
+}
+
+__global__ void iota_kernel(uint32_t *p, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)i;
+}
+
+// S3: one hooking round over the surviving links.
+__global__ void hook_kernel(const uint32_t *__restrict__ ea, const uint32_t *__restrict__ eb,
+                            const double *__restrict__ es, int64_t m, double two_ds, uint32_t *parent,
+                            uint32_t *changed)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (!(es[e] >= two_ds)) continue;
+        const uint32_t ra = find_root(parent, ea[e]), rb = find_root(parent, eb[e]);
+        if (ra == rb) continue;
+        atomicMin(&parent[max(ra, rb)], min(ra, rb));
+        *changed = 1u;
+    }
+}
+
+__global__ void compress_kernel(uint32_t *parent, int64_t C)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x)
+        parent[c] = find_root(parent, (uint32_t)c);
+}
+
+// S4: count, density sum and peak key of every component's members.
+__global__ void member_stats_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc,
+                                    int64_t n, float ds, const uint32_t *__restrict__ parent,
+                                    unsigned long long *__restrict__ cnt, double *__restrict__ sum,
+                                    unsigned long long *__restrict__ pkey)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        uint32_t r = kNone;
+        uint64_t k = 0;
+        if (i < n) {
+            k = dkey[i];
+            const uint32_t c = pc[i];
+            if (c != kNone && key_dens(k) >= ds) r = parent[c];
+        }
+        const uint32_t active = __ballot_sync(0xffffffffu, r != kNone);
+        if (r == kNone) continue;
+        const uint32_t peers = __match_any_sync(active, r);
+        const double s = peer_sum_f64(peers, (double)key_dens(k));
+        const unsigned long long best = peer_max(peers, k);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicAdd(&cnt[r], (unsigned long long)__popc(peers));
+            atomicAdd(&sum[r], s);
+            atomicMax(&pkey[r], best);
+        }
+    }
+}
+
+// S5: the significance cut, in the same fp64 operations as the definition.
+__global__ void accept_kernel(int64_t C, const uint32_t *__restrict__ parent,
+                              const unsigned long long *__restrict__ cnt, const double *__restrict__ sum,
+                              double ds, long long n_min, double f, uint32_t *__restrict__ flag)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t ok = 0;
+        const unsigned long long k = cnt[c];
+        if (parent[c] == (uint32_t)c && k > 0 && (long long)k >= n_min) {
+            const double N = (double)k;
+            const double mean = __ddiv_rn(sum[c], N);
+            const double thr = __dmul_rn(ds, __dadd_rn(1.0, __ddiv_rn(f, __dsqrt_rn(N))));
+            ok = mean >= thr ? 1u : 0u;
+        }
+        flag[c] = ok;
+    }
+}
+
+__global__ void list_kernel(int64_t C, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+                            const unsigned long long *__restrict__ pkey, uint64_t *__restrict__ gk,
+                            uint32_t *__restrict__ gv)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[c]) continue;
+        gk[pos[c]] = ~(uint64_t)pkey[c];   // ascending = peak density desc, index asc
+        gv[pos[c]] = (uint32_t)c;
+    }
+}
+
+__global__ void rank_kernel(int64_t G, const uint32_t *__restrict__ gv, uint32_t *__restrict__ rank)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x)
+        rank[gv[g]] = (uint32_t)g;
+}
+
+__global__ void label_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc, int64_t n,
+                             float ds, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ flag,
+                             const uint32_t *__restrict__ rank, int32_t *__restrict__ sub)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = -1;
+        const uint32_t c = pc[i];
+        if (c != kNone && key_dens(dkey[i]) >= ds) {
+            const uint32_t r = parent[c];
+            if (flag[r]) g = (int32_t)rank[r];
+        }
+        sub[i] = g;
+    }
+}
+
+inline int grid_for(hop_ctx *c, int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
+    return (int)std::max<int64_t>(b, 1);
+}
+
+inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
+             int n_merge, float d_o, const float *levels, int L, int64_t n_min, double f, int32_t *sub,
+             int64_t *n_sub)
+{
+    // S1
+    HOP_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+    uint64_t *ek;
+    double *es;
+    int64_t m;
+    int rc = boundaries_table(c, chain, dkey, nbr, ld, n, n_merge, d_o, &ek, &es, &m, true);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+    // S2
+    uint32_t *hp = (uint32_t *)c->h_pinned;
+    uint32_t *misc = (uint32_t *)ctx_buf(c, S_MISC, 256);
+    uint32_t *cid = (uint32_t *)ctx_buf(c, S_SUB, (size_t)(2 * n + 64) * sizeof(uint32_t));
+    if (!misc || !cid) return HOP_ENOMEM;
+    uint32_t *pc = cid + ((n + 1 + 63) & ~int64_t(63));
+    uint32_t *d_total = misc, *d_changed = misc + 1;
+    HOP_CUDA(c, cudaMemsetAsync(misc, 0, 16, c->stream));
+    root_flag_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, c->d_err);
+    HOP_LAUNCH(c);
+    rc = scan_exclusive_u32(c, cid, cid, n, d_total);
+    if (rc) return rc;
+    particle_chain_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, pc, c->d_err);
+    HOP_LAUNCH(c);
+    HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 4, cudaMemcpyDeviceToHost, c->stream));
+    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int64_t C = hp[0];
+    // arrays over chains (C) and symmetric boundaries (m)
+    const int64_t Cp = std::max<int64_t>(C, 1), mp = std::max<int64_t>(m, 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    const size_t o_parent = take(Cp * 4), o_cnt = take(Cp * 8), o_sum = take(Cp * 8), o_pkey = take(Cp * 8),
+                 o_flag = take((Cp + 1) * 4), o_pos = take((Cp + 1) * 4), o_rank = take(Cp * 4),
+                 o_ea = take(mp * 4), o_eb = take(mp * 4), o_gk = take(Cp * 8), o_gkb = take(Cp * 8),
+                 o_gv = take(Cp * 4), o_gvb = take(Cp * 4), o_tmp = take(radix_sort_scratch_bytes(Cp));
+    char *base = (char *)ctx_buf(c, S_SUB_C, off);
+    if (!base) return HOP_ENOMEM;
+    uint32_t *parent = (uint32_t *)(base + o_parent), *flag = (uint32_t *)(base + o_flag),
+             *gpos = (uint32_t *)(base + o_pos), *rank = (uint32_t *)(base + o_rank),
+             *ea = (uint32_t *)(base + o_ea), *eb = (uint32_t *)(base + o_eb);
+    unsigned long long *cnt = (unsigned long long *)(base + o_cnt), *pkey = (unsigned long long *)(base + o_pkey);
+    double *sum = (double *)(base + o_sum);
+    uint64_t *gk0 = (uint64_t *)(base + o_gk), *gkb0 = (uint64_t *)(base + o_gkb);
+    uint32_t *gv0 = (uint32_t *)(base + o_gv), *gvb0 = (uint32_t *)(base + o_gvb);
+    void *tmp = base + o_tmp;
+    if (m > 0) {
+        edge_ids_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ek, m, n, chain, dkey, d_o, cid, ea, eb, c->d_err);
+        HOP_LAUNCH(c);
+    }
+    rc = ctx_check_device_error(c);
+    if (rc) return rc;
+    c->stats.n_chains = C;
+    c->stats.n_edges = m;
+    for (int l = 0; l < L; ++l) {
+        const float ds = levels[l];
+        int32_t *out = sub + (int64_t)l * n;
+        if (C == 0) {
+            HOP_CUDA(c, cudaMemsetAsync(out, 0xFF, n * sizeof(int32_t), c->stream));
+            n_sub[l] = 0;
+            continue;
+        }
+        // S3
+        iota_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+        HOP_LAUNCH(c);
+        int rounds = 0;
+        for (; m > 0 && rounds < kMaxRounds; ++rounds) {
+            HOP_CUDA(c, cudaMemsetAsync(d_changed, 0, 4, c->stream));
+            hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ea, eb, es, m, 2.0 * (double)ds, parent, d_changed);
+            HOP_LAUNCH(c);
+            compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+            HOP_LAUNCH(c);
+            HOP_CUDA(c, cudaMemcpyAsync(hp + 1, d_changed, 4, cudaMemcpyDeviceToHost, c->stream));
+            HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (!hp[1]) break;
+        }
+        if (rounds >= kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "subhalo components did not converge");
+        // S4
+        HOP_CUDA(c, cudaMemsetAsync(cnt, 0, C * 8, c->stream));
+        HOP_CUDA(c, cudaMemsetAsync(sum, 0, C * 8, c->stream));
+        HOP_CUDA(c, cudaMemsetAsync(pkey, 0, C * 8, c->stream));
+        member_stats_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, cnt, sum, pkey);
+        HOP_LAUNCH(c);
+        // S5
+        accept_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, cnt, sum, (double)ds, (long long)n_min, f,
+                                                             flag);
+        HOP_LAUNCH(c);
+        rc = scan_exclusive_u32(c, flag, gpos, C, d_total);
+        if (rc) return rc;
+        HOP_CUDA(c, cudaMemcpyAsync(hp, d_total, 4, cudaMemcpyDeviceToHost, c->stream));
+        HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int64_t G = hp[0];
+        if (G > 0) {
+            list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, pkey, gk0, gv0);
+            HOP_LAUNCH(c);
+            uint64_t *gk = gk0, *gkb = gkb0;
+            uint32_t *gv = gv0, *gvb = gvb0;
+            rc = radix_sort_u64(c, gk, gkb, gv, gvb, G, 0, 64, tmp);
+            if (rc) return rc;
+            rank_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, gv, rank);
+            HOP_LAUNCH(c);
+        }
+        label_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, flag, rank, out);
+        HOP_LAUNCH(c);
+        n_sub[l] = G;
+    }
+    return HOP_OK;
+}
+
+}  // namespace
+
+extern "C" int hop_subhalos(hop_ctx *c, const uint32_t *chain, const float *dens, const uint32_t *nbr,
+                            int32_t ld_nbr, int64_t n, int32_t n_merge, float delta_outer, const float *levels,
+                            int32_t n_levels, int64_t n_min, double f_poisson, int32_t *sub, int64_t *n_sub)
+{
+    if (!c) return HOP_EINVAL;
+    c->err.clear();
+    if (!chain || !dens || !nbr || !sub || !n_sub || !levels || n <= 0 || n_levels <= 0)
+        return ctx_fail(c, HOP_EINVAL, "chain, dens, nbr, levels, sub, n_sub, n > 0 and n_levels > 0 are required");
+    if (n >= (int64_t(1) << 31) - 1) return ctx_fail(c, HOP_EINVAL, "n must be < 2^31 - 1");
+    if (n_merge < 1 || n_merge > ld_nbr) return ctx_fail(c, HOP_EINVAL, "n_merge must be in [1, ld_nbr]");
+    if (n_min < 1) return ctx_fail(c, HOP_EINVAL, "n_min must be >= 1");
+    if (!(f_poisson >= 0.0) || !std::isfinite(f_poisson)) return ctx_fail(c, HOP_EINVAL, "f_poisson must be >= 0");
+    for (int l = 0; l < n_levels; ++l)
+        if (!std::isfinite(levels[l]) || !(levels[l] >= delta_outer))
+            return ctx_fail(c, HOP_EINVAL, "every level must be finite and >= delta_outer");
+    HOP_CUDA(c, cudaSetDevice(c->device));
+    const int64_t launches0 = c->launches;
+    HOP_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+    uint64_t *dkey = (uint64_t *)ctx_buf(c, S_DKEY, n * sizeof(uint64_t));
+    if (!dkey) return HOP_ENOMEM;
+    int rc = make_dkey(c, dens, nullptr, n, dkey);
+    if (rc) return rc;
+    rc = subhalos(c, chain, dkey, nbr, ld_nbr, n, n_merge, delta_outer, levels, n_levels, n_min, f_poisson, sub,
+                  n_sub);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+    const int e = ctx_check_device_error(c);
+    float ms = 0.f, ms_b = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) != cudaSuccess) cudaGetLastError();
+    if (cudaEventElapsedTime(&ms_b, c->ev[2], c->ev[3]) != cudaSuccess) cudaGetLastError();
+    c->stats.ms_total = ms;
+    c->stats.ms_boundaries = ms_b;
+    c->stats.ms_merge = ms - ms_b;
+    c->stats.launches = c->launches - launches0;
+    return e;
+}

@@ -184,6 +184,35 @@ def plummer_pair(n_per: int = 1500, a: float = 0.01, sep: float = 0.04, n_backgr
     return pos, cen
 
 
+def chain_graph_case(n: int, n_merge: int, n_chains: int, seed: int, mutual: bool = False):
+    """A random chain structure for the merging stages, without positions:
+    (chain int32 [n], dens float64 [n] holding float32 values, rows int32
+    [n, n_merge]).  n_chains roots, each the densest member of its chain
+    (hops climb); densities gamma-distributed around 120; rows hold the
+    particle itself first, then random particles (with ``mutual``, n_merge - 1
+    random pairings, so that every link has its reverse)."""
+    rng = np.random.default_rng(seed)
+    dens = np.round(rng.gamma(2.0, 60.0, n), 1).astype(np.float32).astype(np.float64)
+    roots = rng.choice(n, n_chains, replace=False)
+    chain = roots[rng.integers(0, n_chains, n)].astype(np.int32)
+    chain[roots] = roots
+    top = np.zeros(n)
+    np.maximum.at(top, chain, dens)
+    dens[roots] = top[roots] + 1.0
+    rows = np.empty((n, n_merge), dtype=np.int32)
+    rows[:, 0] = np.arange(n)
+    if mutual:
+        for t in range(1, n_merge):
+            p = rng.permutation(n)
+            partner = np.empty(n, dtype=np.int32)
+            partner[p[0::2]] = p[1::2]
+            partner[p[1::2]] = p[0::2]
+            rows[:, t] = partner
+    else:
+        rows[:, 1:] = rng.integers(0, n, (n, n_merge - 1))
+    return chain, dens, rows
+
+
 def _nfw_mu(x):
     return np.log1p(x) - x / (1.0 + x)
 

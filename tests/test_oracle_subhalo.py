@@ -73,28 +73,7 @@ def test_example_poisson_cut(ex):
 
 
 def _random_case(n, n_merge, n_chains, seed, mutual=False):
-    rng = np.random.default_rng(seed)
-    dens = np.round(rng.gamma(2.0, 60.0, n), 1)
-    roots = rng.choice(n, n_chains, replace=False)
-    chain = roots[rng.integers(0, n_chains, n)].astype(np.int32)
-    chain[roots] = roots
-    # a root is the densest member of its chain (hops climb)
-    for r in roots:
-        m = chain == r
-        dens[r] = dens[m].max() + 1.0
-    rows = np.empty((n, n_merge), dtype=np.int32)
-    rows[:, 0] = np.arange(n)
-    if mutual:
-        # n_merge - 1 random pairings: every link has its reverse
-        for t in range(1, n_merge):
-            p = rng.permutation(n)
-            partner = np.empty(n, dtype=np.int32)
-            partner[p[0::2]] = p[1::2]
-            partner[p[1::2]] = p[0::2]
-            rows[:, t] = partner
-    else:
-        rows[:, 1:] = rng.integers(0, n, (n, n_merge - 1))
-    return chain, dens, rows
+    return synth.chain_graph_case(n, n_merge, n_chains, seed, mutual)
 
 
 def _brute_sym(chain, dens, rows, d_o):
