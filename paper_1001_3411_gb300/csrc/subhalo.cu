@@ -43,7 +43,7 @@ __device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x
 }
 
 // S2: roots above delta_outer; chain labels must be roots of [0, n).
-__global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+__global__ void sub_root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
                                  int64_t n, float d_o, uint32_t *__restrict__ flag, uint32_t *__restrict__ err)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -57,7 +57,7 @@ __global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint6
 // Per particle above delta_outer: its root's dense id.  A particle above
 // delta_outer has a root above it (hops go uphill); anything else is an
 // inconsistent input.
-__global__ void particle_chain_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
+__global__ void sub_particle_chain_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
                                       int64_t n, float d_o, const uint32_t *__restrict__ cid,
                                       uint32_t *__restrict__ pc, uint32_t *__restrict__ err)
 {
@@ -73,7 +73,7 @@ __global__ void particle_chain_kernel(const uint32_t *__restrict__ chain, const 
     }
 }
 
-__global__ void edge_ids_kernel(const uint64_t *__restrict__ ekey, int64_t m, int64_t n,
+__global__ void sub_edge_ids_kernel(const uint64_t *__restrict__ ekey, int64_t m, int64_t n,
                                 const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey, float d_o,
                                 const uint32_t *__restrict__ cid, uint32_t *__restrict__ ea,
                                 uint32_t *__restrict__ eb, uint32_t *__restrict__ err)
@@ -92,7 +92,7 @@ __global__ void edge_ids_kernel(const uint64_t *__restrict__ ekey, int64_t m, in
     }
 }
 
-__global__ void iota_kernel(uint32_t *p, int64_t n)
+__global__ void sub_iota_kernel(uint32_t *p, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -100,7 +100,7 @@ __global__ void iota_kernel(uint32_t *p, int64_t n)
 }
 
 // S3: one hooking round over the surviving links.
-__global__ void hook_kernel(const uint32_t *__restrict__ ea, const uint32_t *__restrict__ eb,
+__global__ void sub_hook_kernel(const uint32_t *__restrict__ ea, const uint32_t *__restrict__ eb,
                             const double *__restrict__ es, int64_t m, double two_ds, uint32_t *parent,
                             uint32_t *changed)
 {
@@ -114,15 +114,17 @@ __global__ void hook_kernel(const uint32_t *__restrict__ ea, const uint32_t *__r
     }
 }
 
-__global__ void compress_kernel(uint32_t *parent, int64_t C)
+__global__ void sub_compress_kernel(uint32_t *parent, int64_t C)
 {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
          c += (int64_t)gridDim.x * blockDim.x)
         parent[c] = find_root(parent, (uint32_t)c);
 }
 
-// S4: count, density sum and peak key of every component's members.
-__global__ void member_stats_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc,
+// S4: count, density sum and peak key of every component's members.  The
+// sum (fp64 atomics, the slow part) is taken only when the significance
+// cut needs it (sum != nullptr).
+__global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc,
                                     int64_t n, float ds, const uint32_t *__restrict__ parent,
                                     unsigned long long *__restrict__ cnt, double *__restrict__ sum,
                                     unsigned long long *__restrict__ pkey)
@@ -140,18 +142,23 @@ __global__ void member_stats_kernel(const uint64_t *__restrict__ dkey, const uin
         const uint32_t active = __ballot_sync(0xffffffffu, r != kNone);
         if (r == kNone) continue;
         const uint32_t peers = __match_any_sync(active, r);
-        const double s = peer_sum_f64(peers, (double)key_dens(k));
+        const double s = sum ? peer_sum_f64(peers, (double)key_dens(k)) : 0.0;
         const unsigned long long best = peer_max(peers, k);
         if ((threadIdx.x & 31) == __ffs(peers) - 1) {
             atomicAdd(&cnt[r], (unsigned long long)__popc(peers));
-            atomicAdd(&sum[r], s);
+            if (sum) atomicAdd(&sum[r], s);
             atomicMax(&pkey[r], best);
         }
     }
 }
 
 // S5: the significance cut, in the same fp64 operations as the definition.
-__global__ void accept_kernel(int64_t C, const uint32_t *__restrict__ parent,
+// With f = 0 the cut is mean >= delta_s, which every set of members passes:
+// each member is >= delta_s, and rounding is monotone, so a running fp64
+// sum of N of them is >= N delta_s (exact for a float32 delta_s and
+// N < 2^29) and the rounded mean is >= delta_s, in any summation order.
+// Then (f = 0 and n < 2^29) sum is nullptr and only the count is tested.
+__global__ void sub_accept_kernel(int64_t C, const uint32_t *__restrict__ parent,
                               const unsigned long long *__restrict__ cnt, const double *__restrict__ sum,
                               double ds, long long n_min, double f, uint32_t *__restrict__ flag)
 {
@@ -160,16 +167,20 @@ __global__ void accept_kernel(int64_t C, const uint32_t *__restrict__ parent,
         uint32_t ok = 0;
         const unsigned long long k = cnt[c];
         if (parent[c] == (uint32_t)c && k > 0 && (long long)k >= n_min) {
-            const double N = (double)k;
-            const double mean = __ddiv_rn(sum[c], N);
-            const double thr = __dmul_rn(ds, __dadd_rn(1.0, __ddiv_rn(f, __dsqrt_rn(N))));
-            ok = mean >= thr ? 1u : 0u;
+            if (!sum) {
+                ok = 1u;
+            } else {
+                const double N = (double)k;
+                const double mean = __ddiv_rn(sum[c], N);
+                const double thr = __dmul_rn(ds, __dadd_rn(1.0, __ddiv_rn(f, __dsqrt_rn(N))));
+                ok = mean >= thr ? 1u : 0u;
+            }
         }
         flag[c] = ok;
     }
 }
 
-__global__ void list_kernel(int64_t C, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+__global__ void sub_list_kernel(int64_t C, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
                             const unsigned long long *__restrict__ pkey, uint64_t *__restrict__ gk,
                             uint32_t *__restrict__ gv)
 {
@@ -181,14 +192,14 @@ __global__ void list_kernel(int64_t C, const uint32_t *__restrict__ flag, const 
     }
 }
 
-__global__ void rank_kernel(int64_t G, const uint32_t *__restrict__ gv, uint32_t *__restrict__ rank)
+__global__ void sub_rank_kernel(int64_t G, const uint32_t *__restrict__ gv, uint32_t *__restrict__ rank)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x)
         rank[gv[g]] = (uint32_t)g;
 }
 
-__global__ void label_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc, int64_t n,
+__global__ void sub_label_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc, int64_t n,
                              float ds, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ flag,
                              const uint32_t *__restrict__ rank, int32_t *__restrict__ sub)
 {
@@ -233,11 +244,11 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
     uint32_t *pc = cid + ((n + 1 + 63) & ~int64_t(63));
     uint32_t *d_total = misc, *d_changed = misc + 1;
     HOP_CUDA(c, cudaMemsetAsync(misc, 0, 16, c->stream));
-    root_flag_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, c->d_err);
+    sub_root_flag_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, c->d_err);
     HOP_LAUNCH(c);
     rc = scan_exclusive_u32(c, cid, cid, n, d_total);
     if (rc) return rc;
-    particle_chain_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, pc, c->d_err);
+    sub_particle_chain_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, pc, c->d_err);
     HOP_LAUNCH(c);
     HOP_CUDA(c, cudaMemcpyAsync(hp, misc, 4, cudaMemcpyDeviceToHost, c->stream));
     HOP_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -261,7 +272,7 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
     uint32_t *gv0 = (uint32_t *)(base + o_gv), *gvb0 = (uint32_t *)(base + o_gvb);
     void *tmp = base + o_tmp;
     if (m > 0) {
-        edge_ids_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ek, m, n, chain, dkey, d_o, cid, ea, eb, c->d_err);
+        sub_edge_ids_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ek, m, n, chain, dkey, d_o, cid, ea, eb, c->d_err);
         HOP_LAUNCH(c);
     }
     rc = ctx_check_device_error(c);
@@ -277,14 +288,14 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
             continue;
         }
         // S3
-        iota_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+        sub_iota_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
         HOP_LAUNCH(c);
         int rounds = 0;
         for (; m > 0 && rounds < kMaxRounds; ++rounds) {
             HOP_CUDA(c, cudaMemsetAsync(d_changed, 0, 4, c->stream));
-            hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ea, eb, es, m, 2.0 * (double)ds, parent, d_changed);
+            sub_hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ea, eb, es, m, 2.0 * (double)ds, parent, d_changed);
             HOP_LAUNCH(c);
-            compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+            sub_compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
             HOP_LAUNCH(c);
             HOP_CUDA(c, cudaMemcpyAsync(hp + 1, d_changed, 4, cudaMemcpyDeviceToHost, c->stream));
             HOP_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -292,14 +303,15 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
         }
         if (rounds >= kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "subhalo components did not converge");
         // S4
+        double *lsum = (f > 0.0 || n >= (int64_t(1) << 29)) ? sum : nullptr;
         HOP_CUDA(c, cudaMemsetAsync(cnt, 0, C * 8, c->stream));
-        HOP_CUDA(c, cudaMemsetAsync(sum, 0, C * 8, c->stream));
+        if (lsum) HOP_CUDA(c, cudaMemsetAsync(lsum, 0, C * 8, c->stream));
         HOP_CUDA(c, cudaMemsetAsync(pkey, 0, C * 8, c->stream));
-        member_stats_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, cnt, sum, pkey);
+        sub_member_stats_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, cnt, lsum, pkey);
         HOP_LAUNCH(c);
         // S5
-        accept_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, cnt, sum, (double)ds, (long long)n_min, f,
-                                                             flag);
+        sub_accept_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, cnt, lsum, (double)ds, (long long)n_min,
+                                                                 f, flag);
         HOP_LAUNCH(c);
         rc = scan_exclusive_u32(c, flag, gpos, C, d_total);
         if (rc) return rc;
@@ -307,16 +319,16 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
         HOP_CUDA(c, cudaStreamSynchronize(c->stream));
         const int64_t G = hp[0];
         if (G > 0) {
-            list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, pkey, gk0, gv0);
+            sub_list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, pkey, gk0, gv0);
             HOP_LAUNCH(c);
             uint64_t *gk = gk0, *gkb = gkb0;
             uint32_t *gv = gv0, *gvb = gvb0;
             rc = radix_sort_u64(c, gk, gkb, gv, gvb, G, 0, 64, tmp);
             if (rc) return rc;
-            rank_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, gv, rank);
+            sub_rank_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, gv, rank);
             HOP_LAUNCH(c);
         }
-        label_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, flag, rank, out);
+        sub_label_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, flag, rank, out);
         HOP_LAUNCH(c);
         n_sub[l] = G;
     }

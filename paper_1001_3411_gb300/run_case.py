@@ -4,7 +4,8 @@ times and counters: a small driver for profilers (ncu) and quick timing.
   python -m paper_1001_3411_gb300.run_case --n 16777216 --radius learned \
       --qpw 4 --cpr 1 --steps 2 [--path batch|eager|single]
 
-``--path batch`` (the default) runs the box as a one-subvolume batched pass
+``--subhalos`` adds the ADAPTAHOP subhalo call (five thresholds) on the
+same box after each pass.  ``--path batch`` (the default) runs the box as a one-subvolume batched pass
 (the CUDA-graph path the benchmark times); ``--path eager`` runs the same
 pass with its kernels enqueued one by one (the same kernels on the same
 data; profilers that cannot look inside a graph with conditional nodes see
@@ -38,6 +39,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--path", choices=["batch", "eager", "single"], default="batch")
     ap.add_argument("--halo", action="store_true", help="also compute the halo statistics of each pass")
+    ap.add_argument("--subhalos", action="store_true",
+                    help="also run hop_run with chains and lists, then ADAPTAHOP subhalos at five thresholds")
     a = ap.parse_args(argv)
     build_library()
     pos, _ = synth.nfw_box(a.n, synth.workload_seed(3))
@@ -60,6 +63,14 @@ def main(argv=None):
         if a.halo:
             h.hop_halo_stats(d, r["dens"], r["group"], ng)
             line["halo_ms"] = h.stats()["ms_total"]
+        if a.subhalos:
+            rs = h.hop_run(d, p, ld_nbr=p.n_hop, want_chain=True)
+            _, n_sub = h.hop_subhalos(rs["chain"], rs["dens"], rs["nbr"], p.n_merge, p.delta_outer,
+                                      [80.0, 160.0, 320.0, 640.0, 1280.0])
+            st = h.stats()
+            line.update(sub_ms=st["ms_total"], sub_boundaries_ms=st["ms_boundaries"],
+                        sub_edges=st["n_edges"], sub_chains=st["n_chains"], n_sub=n_sub.tolist())
+            del rs
         print(json.dumps(line), flush=True)
     h.close()
 
