@@ -2,7 +2,7 @@
 times and counters: a small driver for profilers (ncu) and quick timing.
 
   python -m paper_1001_3411_gb300.run_case --n 16777216 --radius learned \
-      --qpw 4 --cpr 1 --steps 2 [--path batch|eager|single]
+      --qpw 4 --cpr 1 --steps 2 [--path batch|eager|single] [--lists 64:16,65:65]
 
 ``--subhalos`` adds the ADAPTAHOP subhalo call (five thresholds) on the
 same box after each pass.  ``--path batch`` (the default) runs the box as a one-subvolume batched pass
@@ -33,7 +33,10 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=16777216)
-    ap.add_argument("--radius", choices=["plain", "count", "learned"], default="learned")
+    ap.add_argument("--radius", default="learned",
+                    help="plain, count or learned; a comma list runs each in turn on the same box")
+    ap.add_argument("--lists", default="64:16",
+                    help="Ndens:Nhop pairs, comma separated (65:65 is the paper's default, Table 2)")
     ap.add_argument("--qpw", type=int, default=4)
     ap.add_argument("--cpr", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -47,11 +50,20 @@ def main(argv=None):
     d = torch.from_numpy(pos).cuda()
     h = Hop(0)
     h.set_tuning(a.qpw, a.cpr)
-    mode = {"plain": 0, "count": 1, "learned": 2}[a.radius]
-    if mode == 2:
+    modes = {"plain": 0, "count": 1, "learned": 2}
+    radii = a.radius.split(",")
+    if "learned" in radii:
         w, m = radius_model.load()[a.qpw]
         h.hop_mlp_load(w, m)
-    p = default_params(radius_mode=mode)
+    for radius in radii:
+        for lst in a.lists.split(","):
+            nd, nh = (int(x) for x in lst.split(":"))
+            p = default_params(radius_mode=modes[radius], n_dens=nd, n_hop=nh)
+            run(a, h, d, p, dict(radius=radius, n_dens=nd, n_hop=nh) if len(radii) > 1 or "," in a.lists else {})
+    h.close()
+
+
+def run(a, h, d, p, tag):
     for i in range(a.steps):
         if a.path in ("batch", "eager"):
             r = h.hop_run_batch(d, [0, a.n], [1.0], p, eager=a.path == "eager")
@@ -59,7 +71,7 @@ def main(argv=None):
         else:
             r = h.hop_run(d, p)
             ng = r["n_groups"]
-        line = dict(step=i, **h.stats())
+        line = dict(step=i, **tag, **h.stats())
         if a.halo:
             h.hop_halo_stats(d, r["dens"], r["group"], ng)
             line["halo_ms"] = h.stats()["ms_total"]
@@ -72,7 +84,6 @@ def main(argv=None):
                         sub_edges=st["n_edges"], sub_chains=st["n_chains"], n_sub=n_sub.tolist())
             del rs
         print(json.dumps(line), flush=True)
-    h.close()
 
 
 if __name__ == "__main__":
