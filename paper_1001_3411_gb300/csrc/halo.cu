@@ -136,13 +136,6 @@ __global__ void halo_rmax_kernel(int64_t G, const unsigned long long *__restrict
         rmax[g] = __longlong_as_double((long long)rbits[g]);
 }
 
-inline int grid_for(hop_ctx *c, int64_t n)
-{
-    int64_t b = (n + 255) / 256;
-    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
-    return (int)std::max<int64_t>(b, 1);
-}
-
 template <typename T>
 int halo_stats_t(hop_ctx *c, const T *pos, const float *dens, const int32_t *group, int64_t n, int64_t G,
                  double box, int64_t *count, uint32_t *peak, double *com, double *rmax)

@@ -213,6 +213,34 @@ __device__ __forceinline__ int seg_of_index(const SegDesc *__restrict__ seg, int
     return lo;
 }
 
+// Grid for a grid-stride loop over n items: 256-thread blocks, at most 32
+// blocks per SM, at least one block.
+inline int grid_for(hop_ctx *c, int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    b = b < (int64_t)c->num_sms * 32 ? b : (int64_t)c->num_sms * 32;
+    return (int)(b > 1 ? b : 1);
+}
+
+// Offsets of arrays packed into one scratch buffer start on 256 bytes.
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Density keys: (density bits << 32) | (0xFFFFFFFF - original index).
+__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ uint32_t key_orig(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
+
+// Root of x in a union-find forest whose parents only point to smaller
+// labels (so every walk ends); the walk is bounded all the same.
+__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x)
+{
+    for (int g = 0; g < (1 << 24); ++g) {
+        const uint32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
 // Warp aggregation for per-group atomics: `peers` is the set of lanes that
 // hold the same group (__match_any_sync); every lane of the set gets the
 // sum or maximum of the set's values, combined in ascending lane order.

@@ -15,8 +15,6 @@ constexpr uint64_t kEmpty = ~0ull;    // no valid pair key has lo == hi == 0xFFF
 constexpr int kMaxProbe = 512;
 constexpr int kChainLimit = 1 << 26;
 
-__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
-
 __global__ void dkey_kernel(const float *__restrict__ dens, const uint32_t *__restrict__ orig,
                             int64_t n, uint64_t *__restrict__ dkey)
 {
@@ -283,13 +281,6 @@ __global__ void gather_f64_kernel(const double *__restrict__ src, const uint32_t
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = src[idx[i]];
-}
-
-inline int grid_for(hop_ctx *c, int64_t n)
-{
-    int64_t b = (n + 255) / 256;
-    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
-    return (int)std::max<int64_t>(b, 1);
 }
 
 }  // namespace

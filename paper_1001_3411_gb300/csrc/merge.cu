@@ -27,9 +27,6 @@ namespace {
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kMaxRounds = 64;
 
-__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
-__device__ __forceinline__ uint32_t key_orig(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
-
 __global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
                                  int64_t n, float d_o, uint32_t *__restrict__ flag,
                                  uint32_t *__restrict__ err)
@@ -124,16 +121,6 @@ __global__ void fill_kernel(uint32_t *p, DevCount nc, uint32_t v)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
-}
-
-__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x)
-{
-    for (int g = 0; g < (1 << 24); ++g) {
-        const uint32_t p = parent[x];
-        if (p == x) return x;
-        x = p;
-    }
-    return x;
 }
 
 __global__ void proto_hook_kernel(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
@@ -315,15 +302,6 @@ __global__ void fill_u64_n_kernel(unsigned long long *p, DevCount nc, unsigned l
         p[i] = v;
 }
 
-inline int grid_for(hop_ctx *c, int64_t n)
-{
-    int64_t b = (n + 255) / 256;
-    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
-    return (int)std::max<int64_t>(b, 1);
-}
-
-inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-
 }  // namespace
 
 int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_t n,
@@ -350,7 +328,7 @@ int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_
     // arrays over chains and edges
     const int64_t Cp = std::max<int64_t>(C, 1), mp = std::max<int64_t>(m, 1);
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     const size_t o_ckey = take(Cp * 8), o_own = take(Cp), o_parent = take(Cp * 4),
                  o_best = take(Cp * 4), o_tgt = take(Cp * 4), o_gpeak = take(Cp * 8),
                  o_flag = take((Cp + 1) * 4), o_grank = take(Cp * 4), o_ea = take(mp * 4),
@@ -510,7 +488,7 @@ int merge_groups_graph(hop_ctx *c, const MergeGraphArgs &a)
     uint32_t *d_round1 = a.counts + 3, *d_round2 = a.counts + 4;
     const DevCount C{Cmax, d_C}, G{Cmax, d_G};
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     const size_t o_cid = take((n + 1) * 4), o_ckey = take(Cmax * 8), o_own = take(Cmax),
                  o_parent = take(Cmax * 4), o_best = take(Cmax * 4), o_tgt = take(Cmax * 4),
                  o_gpeak = take(Cmax * 8), o_flag = take((Cmax + 1) * 4), o_grank = take(Cmax * 4),

@@ -30,18 +30,6 @@ namespace {
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kMaxRounds = 64;
 
-__device__ __forceinline__ float key_dens(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
-
-__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x)
-{
-    for (int g = 0; g < (1 << 24); ++g) {
-        const uint32_t p = parent[x];
-        if (p == x) return x;
-        x = p;
-    }
-    return x;
-}
-
 // S2: roots above delta_outer; chain labels must be roots of [0, n).
 __global__ void sub_root_flag_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
                                  int64_t n, float d_o, uint32_t *__restrict__ flag, uint32_t *__restrict__ err)
@@ -215,15 +203,6 @@ __global__ void sub_label_kernel(const uint64_t *__restrict__ dkey, const uint32
     }
 }
 
-inline int grid_for(hop_ctx *c, int64_t n)
-{
-    int64_t b = (n + 255) / 256;
-    b = std::min<int64_t>(b, (int64_t)c->num_sms * 32);
-    return (int)std::max<int64_t>(b, 1);
-}
-
-inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-
 int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
              int n_merge, float d_o, const float *levels, int L, int64_t n_min, double f, int32_t *sub,
              int64_t *n_sub)
@@ -256,7 +235,7 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
     // arrays over chains (C) and symmetric boundaries (m)
     const int64_t Cp = std::max<int64_t>(C, 1), mp = std::max<int64_t>(m, 1);
     size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     const size_t o_parent = take(Cp * 4), o_cnt = take(Cp * 8), o_sum = take(Cp * 8), o_pkey = take(Cp * 8),
                  o_flag = take((Cp + 1) * 4), o_pos = take((Cp + 1) * 4), o_rank = take(Cp * 4),
                  o_ea = take(mp * 4), o_eb = take(mp * 4), o_gk = take(Cp * 8), o_gkb = take(Cp * 8),
