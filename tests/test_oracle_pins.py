@@ -104,12 +104,14 @@ def test_density_kernel_shape_is_the_cubic_bspline():
     assert dens == pytest.approx(expect, rel=1e-9)
 
 
-def test_density_poisson_closed_form():
+@pytest.mark.parametrize("k", [64, 65, 16])
+def test_density_poisson_closed_form(k):
     """Uniform points in a periodic unit box: conditional on r_k the k-2 inner
     neighbours are uniform in the ball, E[w] over the ball is 3/32 (from the
     kernel's unit normalisation), W(0) = 8/(pi r_k^3), and E[1/V_k] =
-    (N-1)/(k-2).  Hence E[delta] = (k - 2 + 32/3)/(k - 2) * (N-1)/N."""
-    n, k = 40000, 64
+    (N-1)/(k-2).  Hence E[delta] = (k - 2 + 32/3)/(k - 2) * (N-1)/N.  k = 65
+    is the paper's own Ndens (Table 2)."""
+    n = 40000
     pos = synth.uniform_box(n, 11)
     _, d2 = oracle.knn(pos, k)
     dens = oracle.density(d2, n)
