@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s end-to-end HOP at 512^3: learned-radius vs plain GPU, same output"
 N_DENS, N_HOP, N_MERGE = 64, 16, 4
 DELTAS = (80.0, 200.0, 240.0)
-FLOP_PER_CANDIDATE = 8          # 3 sub + 1 mul + 2 fma, counted as in the survey
+FLOP_PER_CANDIDATE = 8          # d^2 of one candidate: 3 sub + 1 mul + 2 fma, an fma counted as 2
 IDEAL_CANDIDATES = N_DENS * 6.0 / math.pi   # stencil sized to the ball
 
 
