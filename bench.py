@@ -52,6 +52,19 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-subvolume section")
     ap.add_argument("--no-subhalos", action="store_true", help="skip the ADAPTAHOP subhalo section")
+    # single-case mode: one box, a few passes, one JSON line of stage times
+    # and counters per pass (the command the profiles/ summaries run under ncu)
+    ap.add_argument("--case", action="store_true", help="run one case and print per-pass stage times")
+    ap.add_argument("--n", type=int, default=16777216, help="--case: particles of the NFW box")
+    ap.add_argument("--radius", default="learned", help="--case: plain, count or learned (comma list)")
+    ap.add_argument("--lists", default="64:16", help="--case: Ndens:Nhop pairs, comma separated")
+    ap.add_argument("--qpw", type=int, default=4, help="--case: queries per warp")
+    ap.add_argument("--cpr", type=int, default=1, help="--case: search cells per radius")
+    ap.add_argument("--path", choices=["batch", "eager", "single"], default="batch",
+                    help="--case: graph-captured batched pass, the same pass enqueued kernel by "
+                         "kernel, or hop_run")
+    ap.add_argument("--halo", action="store_true", help="--case: also time the halo statistics")
+    ap.add_argument("--subhalos", action="store_true", help="--case: also time ADAPTAHOP subhalos")
     return ap.parse_args()
 
 
@@ -107,23 +120,31 @@ def gpu_index(local_rank: int) -> int:
     return local_rank
 
 
-def knn_traffic_per_particle():
-    """DRAM bytes per particle of the kNN kernel from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "knn_traffic.json")
+
+
+def source_hashes(files):
+    """sha256 (first 16 hex digits) of each source file, by repo-relative path."""
     import hashlib
-    import re
+    out = {}
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            out[f] = hashlib.sha256(fh.read()).hexdigest()[:16]
+    return out
+
+
+def knn_traffic_per_particle():
+    """DRAM bytes per particle of the kNN kernel from the committed ncu
+    capture record, or None when any source file the kernel is compiled from
+    changed since that capture."""
     try:
-        txt = open(os.path.join(ROOT, "profiles", "knn_kernel_nfw16M_learned.md")).read()
-        src = open(os.path.join(ROOT, "paper_1001_3411_gb300", "csrc", "knn.cu"), "rb").read()
-    except OSError:
+        rec = json.load(open(TRAFFIC_RECORD))
+        now = source_hashes(rec["sources"].keys())
+    except (OSError, ValueError, KeyError):
         return None, "no capture"
-    want = re.search(r"knn_source_sha256_16: ([0-9a-f]+)", txt)
-    per = re.search(r"traffic_bytes_per_particle: ([0-9.]+)", txt)
-    if not want or not per:
-        return None, "no capture"
-    if hashlib.sha256(src).hexdigest()[:16] != want.group(1):
-        return None, "kernel changed since the ncu capture"
-    return float(per.group(1)), "ncu dram__bytes_read+write on the 16.8M-particle case, scaled by particles"
+    if now != rec["sources"]:
+        return None, "kernel sources changed since the ncu capture"
+    return float(rec["traffic_bytes_per_particle"]), rec["basis"]
 
 
 def measured_peaks():
@@ -173,6 +194,21 @@ def oracle_rate(pos, seconds: float, seed: int = 7):
                        f"box ({t_knn:.1f} s), plus link/boundaries/merge timed per particle on the "
                        f"32,768-particle Plummer set ({t_rest * 1e3:.0f} ms)"),
             "seconds": t_knn + t_rest}
+
+
+def oracle_rate_single_thread(seconds: float):
+    """The oracle on one host core, on a sample of the 256^3 box: the
+    per-core figure of the CPU baseline."""
+    import oracle
+    import synth
+    pos = synth.workload("nfw256")
+    before = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        r = oracle_rate(pos, seconds, seed=11)
+    finally:
+        oracle.set_threads(before)
+    return {"value": r["value"], "unit": "particles/s", "cores": 1, "sample": r["sample"]}
 
 
 # ------------------------------------------------------------- gb300 arm
@@ -368,15 +404,26 @@ def run_gb300(args):
     def step(name):
         return lambda: call(name, dpos, out)
 
-    # identical output across radius policies (untimed check): group ids
-    # compared whole, density bits through their sum
+    # identical output across radius policies (untimed check): group ids,
+    # densities and the Nhop neighbour lists compared element by element
     ref = {}
     for name in ("plain", "learned", "count"):
         configure(name)
-        ng = call(name, dpos, out)
-        ref[name] = (out["group"].clone(), int(out["dens"].view(torch.int32).sum(dtype=torch.int64)), ng)
-    same = all(torch.equal(ref["plain"][0], ref[k][0]) and ref["plain"][1:] == ref[k][1:]
+        if single:
+            r = hop.hop_run(dpos, params[name], ld_nbr=N_HOP)
+            ng = int(r["n_groups"])
+        else:
+            r = hop.hop_run_batch(dpos, off, boxes, params[name], ld_nbr=N_HOP)
+            ng = int(r["n_groups"][0])
+        ref[name] = (r["group"], r["dens"], r["nbr"], ng)
+        del r
+    same = all(torch.equal(ref["plain"][0], ref[k][0]) and torch.equal(ref["plain"][1], ref[k][1])
+               and torch.equal(ref["plain"][2], ref[k][2]) and ref["plain"][3] == ref[k][3]
                for k in ("learned", "count"))
+    group_ref = ref["plain"][0].cpu()
+    n_groups_ref = ref["learned"][3]
+    del ref
+    torch.cuda.empty_cache()
 
     results = {}
     clocks = {}
@@ -466,7 +513,7 @@ def run_gb300(args):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    assert torch.equal(hout["group"], ref["plain"][0].cpu()), "host-buffer run differs"
+    assert torch.equal(hout["group"], group_ref), "host-buffer run differs"
     del hpos, hout
 
     batch = batch_section(hop, args, dist) if not args.no_batch else None
@@ -507,7 +554,7 @@ def run_gb300(args):
                               for k, v in tuned.items()},
                    "radius_model": model_src},
         "identical_output": bool(same),
-        "n_groups": ref["learned"][2],
+        "n_groups": n_groups_ref,
         "plain": {"value": n * world / (ms_p * 1e-3), "ms_per_step": ms_p, "stages_ms": stage(st_p),
                   "candidates_per_particle": st_p[-1]["candidates"] / n,
                   "retries": st_p[-1]["retries"], "searches": st_p[-1]["searches"]},
@@ -518,6 +565,10 @@ def run_gb300(args):
                     "retries": last["retries"], "searches": last["searches"]},
         "single_call_hop_run": {"value": n * world / (ms_single * 1e-3), "ms_per_step": ms_single},
         "speedup_learned_vs_plain": ms_p / ms_l,
+        "speedup_learned_vs_count": ms_c / ms_l,
+        "ablation": ("plain: the first radius is the mean-density Ndens-th-neighbour distance, "
+                     "then certified stencil expansion; count: the closed-form radius from the 27 "
+                     "stencil counts, the non-learned policy closest to the network"),
         "roofline": {"kernel": "knn_kernel<float,P,SEG> (kNN + M4 density)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": (tpp * n if tpp else None),
@@ -536,11 +587,62 @@ def run_gb300(args):
     }
     if rank == 0:
         line["cpu_baseline"] = oracle_rate(pos, args.cpu_seconds)
+        line["cpu_baseline"]["single_thread_nfw256"] = oracle_rate_single_thread(args.cpu_seconds / 4)
         print(json.dumps(line), flush=True)
     hop.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------- single case
+def run_case(args):
+    """One NFW box (the 512^3 generator and seed at --n particles), each
+    radius policy and list length in turn, --steps passes each; one JSON line
+    of stage times and counters per pass.  This is the command the ncu
+    summaries under profiles/ were captured with: --path eager enqueues the
+    batched pass kernel by kernel (ncu cannot look inside a graph with
+    conditional nodes), --path batch replays the graph, --path single calls
+    hop_run."""
+    import torch
+
+    import synth
+    from paper_1001_3411_gb300 import Hop, build_library, default_params, radius_model
+    build_library()
+    pos, _ = synth.nfw_box(args.n, synth.workload_seed(3))
+    d = torch.from_numpy(pos).cuda()
+    h = Hop(0)
+    h.set_tuning(args.qpw, args.cpr)
+    modes = {"plain": 0, "count": 1, "learned": 2}
+    radii = args.radius.split(",")
+    if "learned" in radii:
+        w, m = radius_model.load()[args.qpw]
+        h.hop_mlp_load(w, m)
+    for radius in radii:
+        for lst in args.lists.split(","):
+            nd, nh = (int(x) for x in lst.split(":"))
+            p = default_params(radius_mode=modes[radius], n_dens=nd, n_hop=nh)
+            for i in range(args.steps):
+                if args.path == "single":
+                    r = h.hop_run(d, p)
+                    ng = int(r["n_groups"])
+                else:
+                    r = h.hop_run_batch(d, [0, args.n], [1.0], p, eager=args.path == "eager")
+                    ng = int(r["n_groups"][0])
+                line = dict(step=i, radius=radius, n_dens=nd, n_hop=nh, **h.stats())
+                if args.halo:
+                    h.hop_halo_stats(d, r["dens"], r["group"], ng)
+                    line["halo_ms"] = h.stats()["ms_total"]
+                if args.subhalos:
+                    rs = h.hop_run(d, p, ld_nbr=p.n_hop, want_chain=True)
+                    _, n_sub = h.hop_subhalos(rs["chain"], rs["dens"], rs["nbr"], p.n_merge, p.delta_outer,
+                                              [80.0, 160.0, 320.0, 640.0, 1280.0])
+                    st = h.stats()
+                    line.update(sub_ms=st["ms_total"], sub_boundaries_ms=st["ms_boundaries"],
+                                sub_edges=st["n_edges"], sub_chains=st["n_chains"], n_sub=n_sub.tolist())
+                    del rs
+                print(json.dumps(line), flush=True)
+    h.close()
 
 
 # --------------------------------------------------------- reference arm
@@ -562,8 +664,11 @@ def run_reference(args):
         oracle_rate(pos, per_step * 0.25, seed=100 + i)
     rates = [oracle_rate(pos, per_step, seed=i) for i in range(args.steps)]
     v = statistics.median(r["value"] for r in rates)
+    # a step is the whole box: its time at the sampled rate
     line = {"metric": METRIC, "value": v, "unit": "particles/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": len(pos) * 1e3 / v,
+            "ms_per_step_basis": "particles of the box / sampled rate (the sample itself took "
+                                 f"{statistics.median(r['seconds'] for r in rates):.1f} s per step)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": wl, "n_particles": len(pos), "n_dens": N_DENS, "n_hop": N_HOP,
@@ -577,7 +682,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gb300(a)

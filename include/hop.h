@@ -57,7 +57,7 @@ enum {
  * particles fall inside a radius whose ball was scanned completely, and is
  * otherwise repeated with a larger radius. */
 enum {
-    HOP_RADIUS_PLAIN = 0,   /* fixed base-grid cell: plain stencil expansion         */
+    HOP_RADIUS_PLAIN = 0,   /* mean-density Ndens-th-neighbour distance, expanded    */
     HOP_RADIUS_COUNT = 1,   /* closed form from the 27 stencil cell counts          */
     HOP_RADIUS_LEARNED = 2  /* the loaded MLP reads the 27 log-counts (hop_mlp_*)   */
 };
@@ -196,8 +196,9 @@ int hop_run(hop_ctx *ctx, const void *pos, int64_t n, const hop_params *params,
  *            and replayed while the subvolumes, parameters, tuning and
  *            buffers stay the same); HOP_BATCH_EAGER: kernels are enqueued
  *            one by one and the merge loops are driven from the host.
- * Queries per warp must be 4, 8 or 16 (hop_set_tuning); with
- * HOP_RADIUS_LEARNED the network loaded for that setting is used.  Stage
+ * Queries per warp must be 4, 8, 16 or 32 (hop_set_tuning; 32 runs one
+ * query per lane); with HOP_RADIUS_LEARNED the network loaded for that
+ * setting is used.  Stage
  * times in hop_stats are those of the pass on the device.  Synchronises the
  * stream.
  */
@@ -223,7 +224,7 @@ int hop_apply_tuning(hop_ctx *ctx, const hop_tuning *t);
  * Times the batched pass (graph replays, median of reps) for each of n_cand
  * candidates on the given batch, writes each candidate's ms, and applies
  * the fastest; *best = its index.  Candidates with a qpw other than 4, 8,
- * 16, or (learned radius) with no network loaded for their qpw, are
+ * 16 or 32, or (learned radius) with no network loaded for their qpw, are
  * skipped.  Results do not depend on the tuning.  Synchronises the stream.
  */
 int hop_autotune(hop_ctx *ctx, const float *pos, const int64_t *offsets, const double *boxes,

@@ -167,7 +167,7 @@ int density_core(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, in
     a.n_out = n_out;
     a.ld_out = st->ld_s;
     a.chunk_r = chunk_r;
-    a.plain_r = plain_radius_for(n, p->box);
+    a.plain_r = plain_radius_for(n, p->box, p->n_dens);
     a.nbr_s = st->nbr_s;
     a.dens_s = st->dens_s;
     a.rk_s = st->rk_s;

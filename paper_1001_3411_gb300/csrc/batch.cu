@@ -170,7 +170,7 @@ int make_plan(hop_ctx *c, const int64_t *offsets, const double *boxes, int B, co
         d.cell0 = cells;
         d.box = box;
         d.norm = box * box * box / ((double)nb * 3.14159265358979323846);
-        d.plain_r = plain_radius_for(nb, box);
+        d.plain_r = plain_radius_for(nb, box, p->n_dens);
         d.level_dense = dense_level_for(nb);
         chunks += (nb + qpw - 1) / qpw;
         cells += (int64_t(1) << (3 * d.level_dense)) + 1;

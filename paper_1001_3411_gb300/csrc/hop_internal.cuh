@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -167,14 +168,14 @@ inline int dense_level_for(int64_t n)
     return l < 10 ? l + 1 : 10;
 }
 
-// First search radius of the plain path: the side of the coarsest grid
-// cell holding fewer than 1024 particles at the box's mean density (the
-// level l with 128 <= n / 8^l < 1024).
-inline float plain_radius_for(int64_t n, double box)
+// First search radius of the plain path: the distance of the k-th nearest
+// neighbour at the box's mean density, the radius of a ball that holds k of
+// the n particles on average: (3 k L^3 / (4 pi n))^(1/3).  The certified
+// search expands it where the ball holds fewer than k.
+inline float plain_radius_for(int64_t n, double box, int k)
 {
-    int lb = 0;
-    while (lb < 15 && (int64_t(1) << (3 * (lb + 1))) * 16 <= n) ++lb;
-    return (float)(box / (double)(1 << lb));
+    const double r = box * cbrt(3.0 * (double)k / (4.0 * 3.14159265358979323846 * (double)n));
+    return (float)r;
 }
 
 // ------------------------------------------------------------ batches ----

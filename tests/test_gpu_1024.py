@@ -3,18 +3,13 @@ background) through hop_density and hop_run in the learned-radius
 configuration: sampled neighbour lists and densities against the oracle's
 brute force over all particles, plus whole-box invariants.
 
-It needs about 200 GB of device memory and several minutes, so it runs only
-when HOP_TEST_1024=1 is set."""
-import os
-
+It needs about 200 GB of device memory and about two minutes."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
-if os.environ.get("HOP_TEST_1024") != "1":
-    pytest.skip("1024^3 case: set HOP_TEST_1024=1 (about 200 GB of device memory)", allow_module_level=True)
 
 import paper_1001_3411_gb300 as hopgpu
 import synth

@@ -1,11 +1,11 @@
-"""Parity at the full workload sizes, in the configuration the benchmark
-times (learned first radius, 4 queries per warp).
+"""Parity at the full workload sizes.
 
-512^3: sampled neighbour lists and densities against the oracle's brute
-force, and the oracle's hops and chains over all 134M particles fed the
-GPU's densities and lists (bit-exact).  256^3: the whole downstream --
-hops, chains, boundary table, merge -- bit-exact against the oracle fed the
-same arrays."""
+512^3, on the benchmark's own path (one-subvolume batched pass, learned
+first radius, autotuned): sampled neighbour lists and densities against the
+oracle's brute force, and the whole downstream over all 134M particles --
+hops, chains, boundary pairs and sums, every group id -- bit-exact against
+the oracle fed the GPU's densities and lists.  256^3 through hop_run: the
+same downstream check."""
 import numpy as np
 import pytest
 
@@ -28,9 +28,12 @@ D_O, D_S, D_P = 80.0, 200.0, 240.0
 def hop():
     hopgpu.build_library()
     h = hopgpu.Hop(0)
+    # one stored network per queries-per-warp setting, so that the
+    # autotuner can try each
+    for q, (w, m) in sorted(radius_model.load().items()):
+        h.set_tuning(q, 1)
+        h.hop_mlp_load(w, m)
     h.set_tuning(4, 1)
-    w, m = radius_model.load()[4]
-    h.hop_mlp_load(w, m)
     yield h
     h.close()
 
@@ -39,27 +42,49 @@ def _learned():
     return hopgpu.default_params(radius_mode=hopgpu.HOP_RADIUS_LEARNED)
 
 
-def test_512cubed_sampled_knn_and_full_linking(hop):
+def test_512cubed_bench_path_whole_downstream_bit_exact(hop):
+    """The benchmark's own path: one-subvolume batched pass, learned radius,
+    the tuning the autotuner picks.  Sampled lists and densities against the
+    oracle's brute force; hops, chains, the boundary table (pairs and sums)
+    and every group id bit-exact against the oracle fed the GPU's arrays."""
     pos = synth.workload("nfw512")
     n = len(pos)
-    r = hop.hop_run(torch.from_numpy(pos).cuda(), _learned(), ld_nbr=16, want_chain=True)
+    d = torch.from_numpy(pos).cuda()
+    p = _learned()
+    cands = [(4, 1, 0), (8, 1, 0), (16, 1, 0), (32, 1, 0)]
+    best, _ = hop.hop_autotune(d, [0, n], [1.0], p, cands, reps=1)
+    assert 0 <= best < len(cands)
+    r = hop.hop_run_batch(d, [0, n], [1.0], p, ld_nbr=16)
     nbr_d = r["nbr"]
-    # every row starts its list with a particle at distance 0: the particle itself
+    # every row holds a particle at distance 0: the particle itself
     rows = torch.arange(n, device="cuda", dtype=torch.int32)
     assert bool((nbr_d == rows[:, None]).any(dim=1).all())
+    _, chain_d = hop.hop_link(r["dens"], nbr_d, 16, want_hop=False)
+    pair_d, s_d = hop.hop_boundaries(chain_d, r["dens"], nbr_d, 4, D_O)
     nbr = nbr_d.cpu().numpy()
     dens = r["dens"].cpu().numpy()
+    group = r["group"].cpu().numpy()
+    n_groups = int(r["n_groups"][0])
+    chain = chain_d.cpu().numpy()
+    pair = pair_d.cpu().numpy()
+    s_gpu = s_d.cpu().numpy()
+    del r, nbr_d, chain_d, pair_d, s_d, d
+    torch.cuda.empty_cache()
     rng = np.random.default_rng(512)
     q = np.concatenate([rng.choice(n, 192, replace=False), [int(np.argmax(dens)), int(np.argmin(dens)),
                                                              0, n - 1]])
     _, d2_o = check_knn_rows(pos, nbr[q], q, 64, name="nfw512")
     check_density(dens[q], d2_o, n, name="nfw512")
-    hop_o, chain_o = oracle.link(dens.astype(np.float64), nbr, 16)
-    assert np.array_equal(r["chain"].cpu().numpy(), chain_o)
-    # a particle above delta_outer in no group must sit in a sub-peak chain
-    g = r["group"].cpu().numpy()
-    assert r["n_groups"] > 10000
-    assert np.all(g[dens < D_O] == -1)
+    o = oracle_downstream(dens, nbr, 16, 4, D_O, D_S, D_P)
+    assert np.array_equal(chain, o["chain"])
+    lo = (pair >> 32).astype(np.int64)
+    hi = (pair & 0xFFFFFFFF).astype(np.int64)
+    assert np.array_equal(lo, o["lo"].astype(np.int64))
+    assert np.array_equal(hi, o["hi"].astype(np.int64))
+    assert np.array_equal(s_gpu, o["s"])
+    assert n_groups == o["n_groups"] and n_groups > 10000
+    assert np.array_equal(group, o["group"])
+    assert np.all(group[dens < D_O] == -1)
 
 
 def test_256cubed_full_downstream_bit_exact(hop):

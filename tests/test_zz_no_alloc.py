@@ -53,13 +53,19 @@ def test_link_static_matches_link_on_two_calls():
 
 
 def test_link_static_rejects_more_than_its_maximum():
+    # Every buffer holds the full n rows, so even if the size check were
+    # lost the kernels would stay inside their buffers: a regression shows
+    # up as a failed assertion, never as an out-of-bounds access.
     L = load_library()
     n = HOP_STATIC_LINK_MAX_N + 1
-    dens = torch.zeros(16, dtype=torch.float32, device="cuda")
-    nbr = torch.zeros((16, 16), dtype=torch.int32, device="cuda")
-    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    dens = torch.zeros(n, dtype=torch.float32, device="cuda")
+    nbr = torch.zeros((n, 16), dtype=torch.int32, device="cuda")
+    hop = torch.zeros(n, dtype=torch.int32, device="cuda")
+    chain = torch.zeros(n, dtype=torch.int32, device="cuda")
     rc = L.hop_link_static(C.c_void_p(dens.data_ptr()), C.c_void_p(nbr.data_ptr()), 16, n, 16,
-                           C.c_void_p(out.data_ptr()), C.c_void_p(out.data_ptr()),
+                           C.c_void_p(hop.data_ptr()), C.c_void_p(chain.data_ptr()),
                            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
     assert rc == HOP_ESTATIC
-    assert torch.count_nonzero(out).item() == 0
+    assert torch.count_nonzero(hop).item() == 0
+    assert torch.count_nonzero(chain).item() == 0
