@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--lists", default="64:16", help="--case: Ndens:Nhop pairs, comma separated")
     ap.add_argument("--qpw", type=int, default=4, help="--case: queries per warp")
     ap.add_argument("--cpr", type=int, default=1, help="--case: search cells per radius")
+    ap.add_argument("--buf", type=int, default=0,
+                    help="--case: candidate-buffer factor (0: count-then-gather kNN kernel; 2-6: "
+                         "single-scan kernel with that many Ndens of buffer per query)")
     ap.add_argument("--path", choices=["batch", "eager", "single"], default="batch",
                     help="--case: graph-captured batched pass, the same pass enqueued kernel by "
                          "kernel, or hop_run")
@@ -612,7 +615,7 @@ def run_case(args):
     pos, _ = synth.nfw_box(args.n, synth.workload_seed(3))
     d = torch.from_numpy(pos).cuda()
     h = Hop(0)
-    h.set_tuning(args.qpw, args.cpr)
+    h.apply_tuning(args.qpw, args.cpr, args.buf)
     modes = {"plain": 0, "count": 1, "learned": 2}
     radii = args.radius.split(",")
     if "learned" in radii:

@@ -335,6 +335,8 @@ struct KnnArgs {
 };
 int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr);
 int knn32_launch(hop_ctx *c, const KnnArgs &a, int cpr);   // knn32.cu: one query per lane, float32
+// knn_cg.cu: count-then-gather, float32, 4, 8 or 16 queries per warp
+int knn_cg_launch(hop_ctx *c, const KnnArgs &a, int qpw, int cpr);
 
 // link.cu
 int make_dkey(hop_ctx *c, const float *dens, const uint32_t *orig, int64_t n, uint64_t *dkey);
