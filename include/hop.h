@@ -143,6 +143,29 @@ int hop_boundaries(hop_ctx *ctx, const uint32_t *chain, const float *dens,
                    int64_t cap, int64_t *n_edges);
 
 /*
+ * The global boundary table of Parallel HOP (Sec. 3): every subvolume builds
+ * its own table (hop_boundaries over the particles it owns), the tables are
+ * gathered, and each chain pair keeps its largest boundary.  This call takes
+ * the gathered list -- pairs may repeat, in any order -- and writes each
+ * distinct pair once with its largest sum, in ascending pair order:
+ *   pair_in  m_in uint64 (lo << 32) | hi, device;  sum_in  m_in float64 >= 0;
+ *   edge_pair, edge_sum, cap, *n_edges  as in hop_boundaries (HOP_ETABLE
+ *   when cap is too small).  Synchronises the stream.
+ */
+int hop_boundaries_reduce(hop_ctx *ctx, const uint64_t *pair_in, const double *sum_in, int64_t m_in,
+                          uint64_t *edge_pair, double *edge_sum, int64_t cap, int64_t *n_edges);
+
+/*
+ * Density normalisation of a subvolume (Parallel HOP Sec. 3).  A subvolume
+ * together with its padding is run as its own problem, but its densities
+ * must be normalised to the mean density of the whole box: later
+ * hop_density / hop_run calls on this context use n_norm in place of their
+ * own n in delta_i = (L^3 / n) sum W (0 restores their own n).  The batched
+ * call keeps each subvolume's own count.
+ */
+int hop_set_norm_count(hop_ctx *ctx, int64_t n_norm);
+
+/*
  * Merging steps 1, 2, 4, 5 (Sec. 2, Fig. 1): chains whose peak density is
  * >= delta_peak are proto-halos; proto-halos whose boundary s >= 2
  * delta_saddle merge, transitively; every other chain joins the proto-halo

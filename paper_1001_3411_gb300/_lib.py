@@ -30,7 +30,8 @@ EXPORTS = ["hop_default_params", "hop_create", "hop_destroy", "hop_set_stream", 
            "hop_set_tuning", "hop_density", "hop_link", "hop_boundaries", "hop_merge", "hop_run",
            "hop_get_stats", "hop_mlp_load", "hop_mlp_get", "hop_mlp_samples", "hop_mlp_forward",
            "hop_mlp_grad", "hop_mlp_train", "hop_link_static", "hop_run_batch", "hop_get_tuning",
-           "hop_apply_tuning", "hop_autotune", "hop_halo_stats", "hop_subhalos"]
+           "hop_apply_tuning", "hop_autotune", "hop_halo_stats", "hop_subhalos", "hop_boundaries_reduce",
+           "hop_set_norm_count"]
 
 
 class HopParams(C.Structure):
@@ -106,6 +107,8 @@ def load_library(path: str = LIB):
             "hop_halo_stats": (C.c_int, [vp, vp, i32, vp, vp, i64, i64, f64, vp, vp, vp, vp]),
             "hop_subhalos": (C.c_int, [vp, vp, vp, vp, i32, i64, i32, f32, vp, i32, i64, f64, vp, vp]),
             "hop_apply_tuning": (C.c_int, [vp, C.POINTER(HopTuning)]),
+            "hop_boundaries_reduce": (C.c_int, [vp, vp, vp, i64, vp, vp, i64, C.POINTER(i64)]),
+            "hop_set_norm_count": (C.c_int, [vp, i64]),
             "hop_autotune": (C.c_int, [vp, vp, vp, vp, i32, P, C.POINTER(HopTuning), i32, i32,
                                        C.POINTER(i32)]),
         }
@@ -225,6 +228,26 @@ class Hop:
         self._check(self.L.hop_boundaries(self.h, _ptr(chain), _ptr(dens), _ptr(nbr), ld, n, n_merge,
                                           float(delta_outer), _ptr(pair), _ptr(s), cap, C.byref(ne)))
         return pair[: ne.value], s[: ne.value]
+
+    def hop_boundaries_reduce(self, pair, s):
+        """Each distinct pair of a gathered boundary list once, with its
+        largest sum, in ascending pair order."""
+        import torch
+        self._sync_stream()
+        m = pair.shape[0]
+        if m:
+            _need(pair, torch.int64, (m,), "pair")
+            _need(s, torch.float64, (m,), "s")
+        dev = torch.device("cuda", self.device)
+        out_p = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
+        out_s = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        ne = C.c_int64(0)
+        self._check(self.L.hop_boundaries_reduce(self.h, _ptr(pair) if m else None, _ptr(s) if m else None, m,
+                                                 _ptr(out_p), _ptr(out_s), max(m, 1), C.byref(ne)))
+        return out_p[: ne.value], out_s[: ne.value]
+
+    def set_norm_count(self, n_norm: int):
+        self._check(self.L.hop_set_norm_count(self.h, int(n_norm)))
 
     def hop_merge(self, chain, dens, pair, s, delta_outer, delta_saddle, delta_peak):
         import torch

@@ -168,6 +168,7 @@ int density_core(hop_ctx *c, const void *pos, int64_t n, const hop_params *p, in
     a.ld_out = st->ld_s;
     a.chunk_r = chunk_r;
     a.plain_r = plain_radius_for(n, p->box, p->n_dens);
+    a.n_norm = c->norm_n;
     a.nbr_s = st->nbr_s;
     a.dens_s = st->dens_s;
     a.rk_s = st->rk_s;
@@ -337,6 +338,31 @@ int hop_link(hop_ctx *c, const float *dens, const uint32_t *nbr, int32_t ld_nbr,
     return hop_links(c, dkey, nbr, ld_nbr, n, n_hop, hop, chain);
 }
 
+// Writes m table entries (ek, es) to the caller's arrays in ascending pair
+// order.  Synchronises the stream.
+static int write_sorted_edges(hop_ctx *c, const uint64_t *ek, const double *es, int64_t m, uint64_t *edge_pair,
+                              double *edge_sum)
+{
+    if (m == 0) return HOP_OK;
+    uint64_t *k1 = (uint64_t *)ctx_buf(c, S_ESORT_K0, m * sizeof(uint64_t));
+    uint64_t *k2 = (uint64_t *)ctx_buf(c, S_ESORT_K1, m * sizeof(uint64_t));
+    uint32_t *v1 = (uint32_t *)ctx_buf(c, S_ESORT_V0, m * sizeof(uint32_t));
+    uint32_t *v2 = (uint32_t *)ctx_buf(c, S_ESORT_V1, m * sizeof(uint32_t));
+    void *tmp = ctx_buf(c, S_ESORT_TMP, radix_sort_scratch_bytes(m));
+    if (!k1 || !k2 || !v1 || !v2 || !tmp) return HOP_ENOMEM;
+    HOP_CUDA(c, cudaMemcpyAsync(k1, ek, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream));
+    int rc = iota_u32(c, v1, m);
+    if (rc) return rc;
+    rc = radix_sort_u64(c, k1, k2, v1, v2, m, 0, 64, tmp);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaMemcpyAsync(edge_pair, k1, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream));
+    // the sums, in the same order
+    rc = gather_f64(c, es, v1, m, edge_sum);
+    if (rc) return rc;
+    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HOP_OK;
+}
+
 int hop_boundaries(hop_ctx *c, const uint32_t *chain, const float *dens, const uint32_t *nbr,
                    int32_t ld_nbr, int64_t n, int32_t n_merge, float delta_outer,
                    uint64_t *edge_pair, double *edge_sum, int64_t cap, int64_t *n_edges)
@@ -360,24 +386,34 @@ int hop_boundaries(hop_ctx *c, const uint32_t *chain, const float *dens, const u
         if (m > cap) return ctx_fail(c, HOP_ETABLE, "edge capacity too small");
         return ctx_fail(c, HOP_EINVAL, "edge_pair and edge_sum are required");
     }
-    if (m == 0) return HOP_OK;
-    // ascending pair order: sort (key, slot) and gather the sums
-    uint64_t *k1 = (uint64_t *)ctx_buf(c, S_ESORT_K0, m * sizeof(uint64_t));
-    uint64_t *k2 = (uint64_t *)ctx_buf(c, S_ESORT_K1, m * sizeof(uint64_t));
-    uint32_t *v1 = (uint32_t *)ctx_buf(c, S_ESORT_V0, m * sizeof(uint32_t));
-    uint32_t *v2 = (uint32_t *)ctx_buf(c, S_ESORT_V1, m * sizeof(uint32_t));
-    void *tmp = ctx_buf(c, S_ESORT_TMP, radix_sort_scratch_bytes(m));
-    if (!k1 || !k2 || !v1 || !v2 || !tmp) return HOP_ENOMEM;
-    HOP_CUDA(c, cudaMemcpyAsync(k1, ek, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream));
-    rc = iota_u32(c, v1, m);
+    return write_sorted_edges(c, ek, es, m, edge_pair, edge_sum);
+}
+
+int hop_boundaries_reduce(hop_ctx *c, const uint64_t *pair_in, const double *sum_in, int64_t m_in,
+                          uint64_t *edge_pair, double *edge_sum, int64_t cap, int64_t *n_edges)
+{
+    if (!c) return HOP_EINVAL;
+    c->err.clear();
+    if (!n_edges || m_in < 0 || (m_in > 0 && (!pair_in || !sum_in))) return ctx_fail(c, HOP_EINVAL, "missing argument");
+    HOP_CUDA(c, cudaSetDevice(c->device));
+    uint64_t *ek;
+    double *es;
+    int64_t m;
+    int rc = edges_max_table(c, pair_in, sum_in, m_in, &ek, &es, &m);
     if (rc) return rc;
-    rc = radix_sort_u64(c, k1, k2, v1, v2, m, 0, 64, tmp);
-    if (rc) return rc;
-    HOP_CUDA(c, cudaMemcpyAsync(edge_pair, k1, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream));
-    // the sums, in the same order
-    rc = gather_f64(c, es, v1, m, edge_sum);
-    if (rc) return rc;
-    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    *n_edges = m;
+    if (m > cap || (m > 0 && (!edge_pair || !edge_sum))) {
+        if (m > cap) return ctx_fail(c, HOP_ETABLE, "edge capacity too small");
+        return ctx_fail(c, HOP_EINVAL, "edge_pair and edge_sum are required");
+    }
+    return write_sorted_edges(c, ek, es, m, edge_pair, edge_sum);
+}
+
+int hop_set_norm_count(hop_ctx *c, int64_t n_norm)
+{
+    if (!c) return HOP_EINVAL;
+    if (n_norm < 0) return ctx_fail(c, HOP_EINVAL, "the normalisation count must be >= 0");
+    c->norm_n = n_norm;
     return HOP_OK;
 }
 

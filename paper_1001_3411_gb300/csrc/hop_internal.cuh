@@ -91,7 +91,8 @@ struct hop_ctx {
     MlpState *mlp = mlp_bank + 3;       // the network of the current setting
     int qpw = 8;                        // kNN queries per warp
     int cpr = 1;                        // search cells per radius
-    int capf = 0;                       // search buffer per query in Ndens (0: 4, or 3 from 8 queries per warp)
+    int capf = 0;                       // kNN kernel choice: 0 count-then-gather, 2-6 single-scan buffer in Ndens
+    int64_t norm_n = 0;                 // hop_set_norm_count: density normalisation count (0: n of the call)
     // graph capture of the batched pass
     bool capturing = false;             // a capture is open on `stream`
     std::vector<void *> graveyard;      // buffers replaced while capturing, freed with the graph
@@ -329,6 +330,7 @@ struct KnnArgs {
     uint32_t *nbr_s;           // n x ld_out sorted indices, or nullptr
     float *dens_s;             // n
     float *rk_s;               // n or nullptr
+    int64_t n_norm = 0;             // particle count of the density normalisation (0: n)
     const SegDesc *seg = nullptr;   // batched pass: subvolume descriptors (device)
     int B = 0;                      // number of subvolumes
     int64_t n_chunks = 0;           // batched pass: total query chunks
@@ -349,6 +351,10 @@ int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, co
                      uint64_t **edge_key, double **edge_sum, int64_t *n_edges, bool symmetric = false);
 int hop_links_async(hop_ctx *c, const uint64_t *dkey, const uint32_t *nbr, int ld, int64_t n,
                     int n_hop, uint32_t *hop, uint32_t *chain);
+// The largest sum per pair of a list of (pair, sum) boundaries with
+// repeated pairs (tables gathered from several subvolumes).
+int edges_max_table(hop_ctx *c, const uint64_t *pair, const double *sum, int64_t m, uint64_t **edge_key,
+                    double **edge_sum, int64_t *n_edges);
 int boundaries_table_async(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey,
                            const uint32_t *nbr, int ld, int64_t n, int n_merge, float delta_outer,
                            int64_t cap, uint32_t *m_dev, unsigned long long *nins,

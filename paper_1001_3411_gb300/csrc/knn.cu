@@ -1080,7 +1080,7 @@ template <typename T, int P, bool SEG> int knn_run(hop_ctx *c, const KnnArgs &a,
     d.chunk_r = a.chunk_r;
     d.plain_r = a.plain_r;
     d.cpr = cpr;
-    d.norm = (T)(a.box * a.box * a.box / ((double)a.n * 3.14159265358979323846));
+    d.norm = (T)(a.box * a.box * a.box / ((double)(a.n_norm > 0 ? a.n_norm : a.n) * 3.14159265358979323846));
     d.nbr_s = a.nbr_s;
     d.dens_s = a.dens_s;
     d.rk_s = a.rk_s;

@@ -741,7 +741,7 @@ template <bool SEG> int knn32_run(hop_ctx *c, const KnnArgs &ka, int cpr)
     d.box = (float)ka.box;
     d.inv_box = (float)(1.0 / ka.box);
     d.half_box = (float)(0.5 * ka.box);
-    d.norm = (float)(ka.box * ka.box * ka.box / ((double)ka.n * 3.14159265358979323846));
+    d.norm = (float)(ka.box * ka.box * ka.box / ((double)(ka.n_norm > 0 ? ka.n_norm : ka.n) * 3.14159265358979323846));
     d.k = ka.k;
     d.n_out = ka.n_out;
     d.ld_out = ka.ld_out;

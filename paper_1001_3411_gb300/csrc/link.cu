@@ -186,6 +186,24 @@ __global__ void boundary_kernel(const uint32_t *__restrict__ chain,
     }
 }
 
+// Inserts a list of (pair, sum) boundaries into the table; each pair keeps
+// its largest sum (the sums are >= 0, so their bits order like the values).
+__global__ void edge_insert_kernel(const uint64_t *__restrict__ pair, const double *__restrict__ sum, int64_t m,
+                                   uint64_t *hkey, unsigned long long *hval, uint64_t mask, uint32_t *err,
+                                   unsigned long long *n_ins)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = pair[e];
+        const double s = sum[e];
+        if (key == kEmpty || !(s >= 0.0)) {
+            atomicOr(err, kErrBadIndex);
+            continue;
+        }
+        if (!table_insert(hkey, hval, mask, key, (unsigned long long)__double_as_longlong(s), n_ins))
+            atomicOr(err, kErrTableFull);
+    }
+}
+
 __global__ void occupied_kernel(const uint64_t *__restrict__ hkey, int64_t cap, uint32_t *__restrict__ occ)
 {
     for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < cap;
@@ -378,6 +396,55 @@ int boundaries_table(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, co
         *edge_key = ek;
         *edge_sum = es;
         *n_edges = m;
+        return HOP_OK;
+    }
+    return ctx_fail(c, HOP_ENOMEM, "boundary table could not be sized");
+}
+
+int edges_max_table(hop_ctx *c, const uint64_t *pair, const double *sum, int64_t m, uint64_t **edge_key,
+                    double **edge_sum, int64_t *n_edges)
+{
+    int64_t cap = 1 << 12;
+    while (cap < 2 * m && cap < (int64_t(1) << 31)) cap <<= 1;
+    unsigned long long *nins = (unsigned long long *)ctx_buf(c, S_MISC, 64);
+    if (!nins) return HOP_ENOMEM;
+    unsigned long long *hn = (unsigned long long *)c->h_pinned;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        uint64_t *hkey = (uint64_t *)ctx_buf(c, S_HKEY, cap * sizeof(uint64_t));
+        unsigned long long *hval = (unsigned long long *)ctx_buf(c, S_HVAL, cap * sizeof(uint64_t));
+        if (!hkey || !hval) return HOP_ENOMEM;
+        fill_u64_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, cap, kEmpty);
+        HOP_LAUNCH(c);
+        HOP_CUDA(c, cudaMemsetAsync(hval, 0, cap * sizeof(uint64_t), c->stream));
+        HOP_CUDA(c, cudaMemsetAsync(nins, 0, 16, c->stream));
+        uint32_t *terr = (uint32_t *)(nins + 1);
+        if (m > 0) {
+            edge_insert_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(pair, sum, m, hkey, hval, (uint64_t)cap - 1,
+                                                                     terr, nins);
+            HOP_LAUNCH(c);
+        }
+        HOP_CUDA(c, cudaMemcpyAsync(hn, nins, 16, cudaMemcpyDeviceToHost, c->stream));
+        HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+        const uint32_t e = *(uint32_t *)((char *)hn + 8);
+        const int64_t u = (int64_t)hn[0];
+        if ((e & kErrBadIndex) != 0) return ctx_fail(c, HOP_EINVAL, "a boundary has an empty key or a negative sum");
+        if ((e & kErrTableFull) != 0) {
+            cap <<= 2;
+            continue;
+        }
+        uint32_t *occ = (uint32_t *)ctx_buf(c, S_EDGE_TMP, (cap + 1) * sizeof(uint32_t));
+        uint64_t *ek = (uint64_t *)ctx_buf(c, S_EDGE_KEY, std::max<int64_t>(u, 1) * sizeof(uint64_t));
+        double *es = (double *)ctx_buf(c, S_EDGE_SUM, std::max<int64_t>(u, 1) * sizeof(double));
+        if (!occ || !ek || !es) return HOP_ENOMEM;
+        occupied_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, cap, occ);
+        HOP_LAUNCH(c);
+        int rc = scan_exclusive_u32(c, occ, occ, cap, nullptr);
+        if (rc) return rc;
+        compact_table_kernel<<<grid_for(c, cap), 256, 0, c->stream>>>(hkey, hval, cap, occ, ek, es);
+        HOP_LAUNCH(c);
+        *edge_key = ek;
+        *edge_sum = es;
+        *n_edges = u;
         return HOP_OK;
     }
     return ctx_fail(c, HOP_ENOMEM, "boundary table could not be sized");
