@@ -129,6 +129,7 @@ struct BatchGraph {
     uint32_t *nbr = nullptr;
     int ld_nbr = 0;
     int64_t table_cap = 0;
+    int64_t chain_cap = 0;
     uint64_t epoch = 0;
     // the graph
     cudaGraph_t graph = nullptr;
@@ -212,7 +213,7 @@ int record(hop_ctx *c, int i)
 // Enqueues the whole pass on the context's stream (captured or not).
 int enqueue_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const PassWords &w,
                  const hop_params *p, const float *dpos, float *dens, int32_t *group, uint32_t *nbr,
-                 int ld_nbr, int64_t table_cap)
+                 int ld_nbr, int64_t table_cap, int64_t chain_cap)
 {
     const int64_t n = pl.n;
     int rc;
@@ -297,6 +298,7 @@ int enqueue_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const Pass
     ma.group = group_s;
     ma.n_groups = w.n_groups;
     ma.counts = w.counts;
+    ma.c_cap = chain_cap;
     if ((rc = merge_groups_graph(c, ma))) return rc;
     if ((rc = record(c, 7))) return rc;
     rc = scatter_outputs(c, perm, n, dens_s, dens, group_s, group, nbr_s, n_out, nbr, ld_nbr,
@@ -369,7 +371,8 @@ int check_batch_params(hop_ctx *c, const hop_params *p)
 // Captures the pass into a new graph (replacing the cached one).
 int capture_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const PassWords &w,
                  const hop_params *p, const float *dpos, float *dens, int32_t *group, uint32_t *nbr,
-                 int ld_nbr, int64_t table_cap, const int64_t *offsets, const double *boxes)
+                 int ld_nbr, int64_t table_cap, int64_t chain_cap, const int64_t *offsets,
+                 const double *boxes)
 {
     graph_drop(c);
     BatchGraph *g = new BatchGraph();
@@ -388,6 +391,7 @@ int capture_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const Pass
     g->nbr = nbr;
     g->ld_nbr = ld_nbr;
     g->table_cap = table_cap;
+    g->chain_cap = chain_cap;
     const int64_t l0 = c->launches;
     if (!c->side) HOP_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     if (!c->cap) HOP_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
@@ -401,7 +405,7 @@ int capture_pass(hop_ctx *c, const BatchPlan &pl, const SegDesc *seg, const Pass
         HOP_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
         c->capturing = true;
         c->graveyard.clear();
-        rc = enqueue_pass(c, pl, seg, w, p, dpos, dens, group, nbr, ld_nbr, table_cap);
+        rc = enqueue_pass(c, pl, seg, w, p, dpos, dens, group, nbr, ld_nbr, table_cap, chain_cap);
         c->capturing = false;
         g->graveyard.swap(c->graveyard);
         e = cudaStreamEndCapture(c->stream, &graph);
@@ -476,14 +480,20 @@ int hop_run_batch(hop_ctx *c, const float *pos, const int64_t *offsets, const do
     HOP_CUDA(c, cudaEventRecord(c->ev[8], c->stream));
     if (host_pos)
         HOP_CUDA(c, cudaMemcpyAsync((void *)dpos, pos, n * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    // capacities of the boundary table and of the merge's chain arrays:
+    // first guesses well above the chain pairs and chains above delta_outer
+    // that halo boxes have (n / 16), grown when the pass reports an overflow
     int64_t cap = int64_t(1) << 12;
-    while (cap < n / 4 && cap < (int64_t(1) << 31)) cap <<= 1;
+    while (cap < n / 16 && cap < (int64_t(1) << 31)) cap <<= 1;
+    int64_t ccap = std::min<int64_t>(n, n / 16 + 65536);
     if (!eager && c->batch && c->batch->table_cap > cap) cap = c->batch->table_cap;
+    if (!eager && c->batch && c->batch->chain_cap > ccap) ccap = c->batch->chain_cap;
     std::vector<uint32_t> hw(16 + B);
     uint32_t herr = 0;
-    for (int attempt = 0; attempt < 4; ++attempt) {
+    for (int attempt = 0; attempt < 6; ++attempt) {
         const bool fresh = eager || !graph_matches(c, c->batch, offsets, boxes, B, p, dpos, dens_dev, group_dev,
-                                                   nbr, ld_nbr) || c->batch->table_cap != cap;
+                                                   nbr, ld_nbr) || c->batch->table_cap != cap ||
+                           c->batch->chain_cap != ccap;
         if (fresh) {
             // descriptors for this plan (the graph reads them at run time)
             HOP_CUDA(c, cudaMemcpyAsync(seg, pl.seg.data(), (size_t)B * sizeof(SegDesc), cudaMemcpyHostToDevice,
@@ -491,11 +501,12 @@ int hop_run_batch(hop_ctx *c, const float *pos, const int64_t *offsets, const do
             HOP_CUDA(c, cudaStreamSynchronize(c->stream));
         }
         if (eager) {
-            rc = enqueue_pass(c, pl, seg, w, p, dpos, dens_dev, group_dev, nbr, ld_nbr, cap);
+            rc = enqueue_pass(c, pl, seg, w, p, dpos, dens_dev, group_dev, nbr, ld_nbr, cap, ccap);
             if (rc) return rc;
         } else {
             if (fresh) {
-                rc = capture_pass(c, pl, seg, w, p, dpos, dens_dev, group_dev, nbr, ld_nbr, cap, offsets, boxes);
+                rc = capture_pass(c, pl, seg, w, p, dpos, dens_dev, group_dev, nbr, ld_nbr, cap, ccap, offsets,
+                                  boxes);
                 if (rc) {
                     graph_drop(c);
                     return rc;
@@ -509,11 +520,13 @@ int hop_run_batch(hop_ctx *c, const float *pos, const int64_t *offsets, const do
                                     cudaMemcpyDeviceToHost, c->stream));
         HOP_CUDA(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
         HOP_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (herr == kErrTableFull && attempt < 3) {
-            // the boundary table overflowed: a larger one, a new capture (the
-            // last attempt keeps the error word for the report below)
+        if ((herr & ~(kErrTableFull | kErrChainCap)) == 0 && herr != 0 && attempt < 5) {
+            // the boundary table or the chain arrays overflowed: larger ones,
+            // a new capture (the last attempt keeps the error word for the
+            // report below)
             HOP_CUDA(c, cudaMemsetAsync(c->d_err, 0, 4, c->stream));
-            cap <<= 2;
+            if (herr & kErrTableFull) cap <<= 2;
+            if (herr & kErrChainCap) ccap = std::min<int64_t>(n, ccap * 4);
             continue;
         }
         break;

@@ -28,6 +28,7 @@ enum : uint32_t {
     kErrTableFull = 1u << 4,    // boundary hash table overflow
     kErrMergeLoop = 1u << 5,    // merge rounds hit their limit
     kErrBadIndex = 1u << 6,     // an index array holds a value >= n
+    kErrChainCap = 1u << 7,     // more chains above delta_outer than a batched pass's merge arrays hold
 };
 
 // Scratch slots owned by a context.  Each slot grows on demand.
@@ -378,6 +379,7 @@ struct MergeGraphArgs {
     int32_t *group;             // n: group rank within the subvolume, -1 = none
     uint32_t *n_groups;         // B (device): groups per subvolume
     uint32_t *counts;           // 8 device words: chains, groups, loop flag, rounds (2)
+    int64_t c_cap = 0;          // chains above delta_outer the merge arrays hold (0: n); more sets kErrChainCap
 };
 int merge_groups_graph(hop_ctx *c, const MergeGraphArgs &a);
 

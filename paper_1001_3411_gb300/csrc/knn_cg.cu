@@ -807,6 +807,1022 @@ __global__ void __launch_bounds__(kCgWarps * 32, 4) knn_cg_kernel(CgDev a)
     }
 }
 
+// ======================================================= one query per warp
+// The same count-then-gather search with the whole warp on one query.  A
+// warp takes a chunk of kWqChunk consecutive particles (whose first radius
+// comes from the radius of that chunk) and serves them one after another.
+// For each query the warp lists the cells (side >= R / cpr, cpr <= 3) that
+// meet its ball, and the lanes read the cells' particles straight from the
+// sorted array -- 32 consecutive particles per step, no shared-memory
+// staging -- with their own histogram rows (32 quarter-octave bins).  The
+// list, the exact Ndens-th distance, the density and the n_out nearest
+// follow as in the grouped kernel above.
+constexpr int kWqChunk = 4;                 // queries per chunk (the radius is per chunk)
+constexpr int kWqBins = 32;                 // histogram bins per lane row
+constexpr int kWqCells = 256;               // cells of one query's region held at once
+
+struct WqSmem {
+    static constexpr size_t cra = 0;                                   // kWqCells range starts
+    static constexpr size_t cln = cra + kWqCells * 4;                  // kWqCells range lengths
+    static constexpr size_t cmd = cln + kWqCells * 4;                  // kWqCells min distance^2 to the query
+    static constexpr size_t cpre = cmd + kWqCells * 4;                 // kWqCells + 1 prefix offsets
+    static constexpr size_t uni = (cpre + (kWqCells + 1) * 4 + 15) & ~size_t(15);
+    static constexpr size_t hist_bytes = (size_t)kWqBins * 32 * 4;
+    __host__ __device__ static size_t ls(int capq) { return uni + (size_t)capq * 4; }
+    __host__ __device__ static size_t kd(int capq) { return uni + (size_t)capq * 8; }
+    __host__ __device__ static size_t od(int capq) { return kd(capq) + kKC * 4; }
+    __host__ __device__ static size_t os(int capq) { return od(capq) + kOC * 4; }
+    __host__ __device__ static size_t total(int capq)
+    {
+        const size_t lists = os(capq) + kOC * 4 - uni;
+        const size_t u = lists > hist_bytes ? lists : hist_bytes;
+        return (uni + u + 15) & ~size_t(15);
+    }
+};
+
+// Bin of the rank-th entry over the 32 histogram rows (lane b sums bin b):
+// the bin (-1 if fewer entries), the entries below it and up to it, and the
+// total.  Uniform over the warp.
+__device__ __forceinline__ void wq_rows_find(const int *hist, int lane, int rank, int &bin, int &below, int &upto,
+                                             int &tot)
+{
+    int mine = 0;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + r];
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += y;
+    }
+    tot = __shfl_sync(kAll, incl, 31);
+    const uint32_t hit = __ballot_sync(kAll, incl - mine < rank && rank <= incl);
+    const int l = hit ? __ffs(hit) - 1 : 0;
+    bin = hit ? l : -1;
+    below = __shfl_sync(kAll, incl - mine, l);
+    upto = __shfl_sync(kAll, incl, l);
+}
+
+// Lists the non-empty cells of level l (frame coordinates) within r of the
+// query; returns their count, or -1 if more than kWqCells meet the ball.
+__device__ int wq_cells(float qx, float qy, float qz, float r, float box, float inv_box, int l,
+                        const uint32_t *__restrict__ cellT, const uint64_t *__restrict__ keys, int level_dense,
+                        uint32_t *cra, uint32_t *cln, float *cmd, int lane, uint32_t lt)
+{
+    const int G = 1 << l;
+    const float sc = inv_box * (float)G, csz = box / (float)G;
+    const float eps = box * 9.5367431640625e-7f;
+    const float r2c = r * r * 1.00001f + box * box * 1e-12f;
+    int c0x = (int)floorf((qx - r) * sc), c0y = (int)floorf((qy - r) * sc), c0z = (int)floorf((qz - r) * sc);
+    int nx = (int)floorf((qx + r) * sc) - c0x + 1, ny = (int)floorf((qy + r) * sc) - c0y + 1,
+        nz = (int)floorf((qz + r) * sc) - c0z + 1;
+    if (nx >= G) { c0x = 0; nx = G; }
+    if (ny >= G) { c0y = 0; ny = G; }
+    if (nz >= G) { c0z = 0; nz = G; }
+    const int ncube = nx * ny * nz;
+    // cell ci of the cube is (ci mod nx, (ci / nx) mod ny, ci / (nx ny)); the
+    // quotients come from float reciprocals, exact for these small integers
+    const float inx = 1.f / (float)nx, inxy = 1.f / (float)(nx * ny);
+    int nkeep = 0;
+    for (int cb = 0; cb < ncube; cb += 32) {
+        const int ci = cb + lane;
+        bool keep = false;
+        uint32_t ra = 0, rb = 0;
+        float md2 = 0.f;
+        if (ci < ncube) {
+            const int cz = (int)(((float)ci + 0.5f) * inxy);
+            const int rxy = ci - cz * nx * ny;
+            const int cy = (int)(((float)rxy + 0.5f) * inx);
+            const int ix = c0x + (rxy - cy * nx), iy = c0y + cy, iz = c0z + cz;
+            const float gx = cg_gap(qx, qx, ix * csz, (ix + 1) * csz, eps);
+            const float gy = cg_gap(qy, qy, iy * csz, (iy + 1) * csz, eps);
+            const float gz = cg_gap(qz, qz, iz * csz, (iz + 1) * csz, eps);
+            md2 = gx * gx + gy * gy + gz * gz;
+            if (md2 <= r2c) {
+                cell_range(cellT, keys, level_dense, l,
+                           morton3((uint32_t)(ix & (G - 1)), (uint32_t)(iy & (G - 1)), (uint32_t)(iz & (G - 1))), ra,
+                           rb);
+                keep = rb > ra;
+            }
+        }
+        const uint32_t bal = __ballot_sync(kAll, keep);
+        const int pos = nkeep + __popc(bal & lt);
+        if (keep && pos < kWqCells) {
+            cra[pos] = ra;
+            cln[pos] = rb - ra;
+            cmd[pos] = md2;
+        }
+        nkeep += __popc(bal);
+    }
+    __syncwarp();
+    return nkeep <= kWqCells ? nkeep : -1;
+}
+
+// Exclusive prefix of the nc cell lengths into cpre[0..nc]; returns the total.
+__device__ __forceinline__ uint32_t wq_prefix(const uint32_t *cln, uint32_t *cpre, int nc, int lane)
+{
+    constexpr int PER = kWqCells / 32;
+    uint32_t v[PER];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int j = lane * PER + i;
+        v[i] = j < nc ? cln[j] : 0u;
+        mine += v[i];
+    }
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - mine;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int j = lane * PER + i;
+        if (j < nc) cpre[j] = run;
+        run += v[i];
+    }
+    const uint32_t total = __shfl_sync(kAll, incl, 31);
+    if (lane == 0) cpre[nc] = total;
+    __syncwarp();
+    return total;
+}
+
+// Visits the particles of cells [0, nc) (ranges cra/cln, prefix cpre), 32
+// consecutive ones per step, lane t taking particle g0 + t: fn(v, s, valid).
+// The cell of each lane's particle comes from the cell starts inside the
+// step's window (one bit each), so no lane searches the prefix.  Four steps
+// issue their loads before the first is used.
+template <typename F>
+__device__ __forceinline__ void wq_visit(const float4 *__restrict__ spos, const uint32_t *cra, const uint32_t *cpre,
+                                         int nc, uint32_t total, int lane, F &&fn)
+{
+    constexpr int U = 4;
+    int cbase = -1;   // the cell holding particle g0 - 1
+    const uint32_t upto_lane = lane == 31 ? kAll : ((2u << lane) - 1u);
+    for (uint32_t g0 = 0; g0 < total; g0 += 32 * U) {
+        uint32_t s[U];
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t w0 = g0 + 32 * u;
+            const int j = cbase + 1 + lane;
+            const uint32_t st = j < nc ? cpre[j] : total;
+            const uint32_t bit = (st >= w0 && st < w0 + 32) ? 1u << (st - w0) : 0u;
+            const uint32_t starts = __reduce_or_sync(kAll, bit);
+            const int c = cbase + __popc(starts & upto_lane);
+            const uint32_t g = w0 + (uint32_t)lane;
+            s[u] = g < total ? cra[c] + (g - cpre[c]) : 0xffffffffu;
+            cbase += __popc(starts);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (s[u] != 0xffffffffu) v[u] = spos[s[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) fn(v[u], s[u], s[u] != 0xffffffffu);
+    }
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
+{
+    using L = WqSmem;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int capq = a.capq;
+    unsigned char *wb = smem_raw + L::total(capq) * wib;
+    uint32_t *cra = (uint32_t *)(wb + L::cra);
+    uint32_t *cln = (uint32_t *)(wb + L::cln);
+    float *cmd = (float *)(wb + L::cmd);
+    uint32_t *cpre = (uint32_t *)(wb + L::cpre);
+    int *hist = (int *)(wb + L::uni);
+    float *Ld = (float *)(wb + L::uni);
+    uint32_t *Ls = (uint32_t *)(wb + L::ls(capq));
+    float *kd = (float *)(wb + L::kd(capq));
+    float *od = (float *)(wb + L::od(capq));
+    uint32_t *os = (uint32_t *)(wb + L::os(capq));
+    const int k = a.k;
+    const int n_out = a.nbr_s ? a.n_out : 0;
+    const int cpr = min(max(a.cpr, 1), 3);
+    unsigned long long cand_acc = 0;
+    uint32_t search_acc = 0, retry_acc = 0, warp_acc = 0;
+
+    for (;;) {
+        unsigned long long ch = 0;
+        if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+        ch = __shfl_sync(kAll, ch, 0);
+        if ((int64_t)ch >= a.n_chunks) break;
+        ++warp_acc;
+        int64_t s_first, n_end, seg_base;
+        float box, half, inv_box, norm, plain_r;
+        const uint32_t *cellT;
+        int level_dense;
+        if constexpr (SEG) {
+            const SegDesc &sd = a.seg[seg_of_chunk(a.seg, a.B, (int64_t)ch)];
+            seg_base = sd.base;
+            n_end = sd.base + sd.n;
+            s_first = sd.base + ((int64_t)ch - sd.chunk0) * kWqChunk;
+            box = (float)sd.box;
+            half = (float)(0.5 * sd.box);
+            inv_box = (float)(1.0 / sd.box);
+            norm = (float)sd.norm;
+            cellT = a.cellT + sd.cell0;
+            level_dense = sd.level_dense;
+            plain_r = sd.plain_r;
+        } else {
+            seg_base = 0;
+            n_end = a.n;
+            s_first = (int64_t)ch * kWqChunk;
+            box = a.box;
+            half = a.half_box;
+            inv_box = a.inv_box;
+            norm = a.norm;
+            cellT = a.cellT;
+            level_dense = a.level_dense;
+            plain_r = a.plain_r;
+        }
+        const int nq = (int)min((int64_t)kWqChunk, n_end - s_first);
+        float R0 = a.chunk_r ? a.chunk_r[ch] : plain_r;
+        if (!(R0 > 0.f)) R0 = box * 1e-6f;
+        for (int qi = 0; qi < nq; ++qi) {
+            const int64_t sq = s_first + qi;
+            const float4 qv = a.spos[sq];
+            const float rqx = qv.x, rqy = qv.y, rqz = qv.z;
+            // ------------- count passes (certify, then refine a crowded bin)
+            float R = R0;
+            int tries = 0, refines = 0;
+            bool certified = false, failed = false, full = false;
+            float qx = rqx, qy = rqy, qz = rqz;
+            bool fx = false, fy = false, fz = false;   // frame shift per axis
+            int nc = 0, l = 1;
+            uint32_t total = 0;
+            int top = 0, shift = kShift0, top0 = 0;
+            float tauA = 0.f;
+            int bk = -1, below_k = 0, upto_k = 0, bk0 = -1, bo = -1, upto_o = 0;
+            float edge_o = -1.f;
+            bool fresh = true;   // the region must be (re)built for R
+            for (;;) {
+                if (fresh) {
+                    ++search_acc;
+                    full = 2.f * R >= half;
+                    // frame: on an axis where the ball crosses a face, coordinates
+                    // >= L/2 move by -L (exact); a whole-box scan takes each
+                    // pair's own minimum image
+                    fx = !full && (rqx - R < 0.f || rqx + R >= box);
+                    fy = !full && (rqy - R < 0.f || rqy + R >= box);
+                    fz = !full && (rqz - R < 0.f || rqz + R >= box);
+                    qx = (fx && rqx >= half) ? rqx - box : rqx;
+                    qy = (fy && rqy >= half) ? rqy - box : rqy;
+                    qz = (fz && rqz >= half) ? rqz - box : rqz;
+                    if (full) {
+                        if (lane == 0) {
+                            cra[0] = (uint32_t)seg_base;
+                            cln[0] = (uint32_t)(n_end - seg_base);
+                            cmd[0] = 0.f;
+                        }
+                        __syncwarp();
+                        nc = 1;
+                    } else {
+                        l = 1;
+                        const float cells = box * (float)cpr / R;   // 2^l <= cells: side >= R / cpr
+                        while (l < kMaxLevel && (float)(1 << (l + 1)) <= cells) ++l;
+                        for (;;) {
+                            nc = wq_cells(qx, qy, qz, R, box, inv_box, l, cellT, a.keys, level_dense, cra, cln, cmd,
+                                          lane, lt);
+                            if (nc >= 0 || l <= 1) break;
+                            --l;   // too many cells meet the ball: take coarser ones
+                        }
+                    }
+                    total = wq_prefix(cln, cpre, nc, lane);
+                    top = top0 = (int)(__float_as_uint(full ? 0.76f * box * box : R * R) >> kShift0);
+                    shift = kShift0;
+                    tauA = full ? INFINITY : R * R;
+                    fresh = false;
+                }
+#pragma unroll 8
+                for (int b = 0; b < kWqBins; ++b) hist[b * 32 + lane] = 0;
+                __syncwarp();
+                {
+                    const int base = top - (kWqBins - 1);
+                    int *hcol = hist + lane;
+                    cand_acc += total;
+                    wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t, bool valid) {
+                        if (!valid) return;
+                        float dx, dy, dz;
+                        if (full) {
+                            dx = wrapdiff(v.x, rqx, box, half);
+                            dy = wrapdiff(v.y, rqy, box, half);
+                            dz = wrapdiff(v.z, rqz, box, half);
+                        } else {
+                            dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
+                            dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
+                            dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
+                        }
+                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (d2 <= tauA) {
+                            const int b = max((int)(__float_as_uint(d2) >> shift) - base, 0);
+                            hcol[b * 32] += 1;
+                        }
+                    });
+                }
+                __syncwarp();
+                int ntot;
+                wq_rows_find(hist, lane, k, bk, below_k, upto_k, ntot);
+                if (!certified) {
+                    if (ntot < k) {
+                        ++retry_acc;
+                        if (++tries >= kCgTries || full) {
+                            if (lane == 0) atomicOr(a.err, kErrKnnRetry);
+                            failed = true;
+                            break;
+                        }
+                        R *= fminf(fmaxf(1.25f, 1.1f * cbrtf((float)k / (float)max(ntot, 1))), 8.f);
+                        fresh = true;
+                        continue;
+                    }
+                    certified = true;
+                    bk0 = bk;
+                    if (n_out > 0) {
+                        int b2, t2;
+                        wq_rows_find(hist, lane, n_out, bo, b2, upto_o, t2);
+                        edge_o = bin_edge(top - (kWqBins - 1), shift, bo);
+                    }
+                }
+                if (upto_k <= capq) break;
+                // a crowded Ndens-th bin: count again in a finer (or lower) window
+                if (++refines > kRefine) {
+                    if (lane == 0) atomicOr(a.err, kErrDegenerate);
+                    failed = true;
+                    break;
+                }
+                const int base = top - (kWqBins - 1);
+                if (bk == 0 && base > 0) {
+                    tauA = fminf(tauA, bin_edge(base, shift, 0));
+                    top -= kWqBins - 1;
+                } else if (shift > 0) {
+                    const int ns = max(shift - 5, 0), d = shift - ns;
+                    tauA = fminf(tauA, bin_edge(base, shift, bk));
+                    top = ((base + bk) << d) | ((1 << d) - 1);
+                    shift = ns;
+                } else {
+                    if (lane == 0) atomicOr(a.err, kErrDegenerate);
+                    failed = true;
+                    break;
+                }
+            }
+            if (failed) continue;
+            const int base = top - (kWqBins - 1);
+            const float edge_k = fminf(bin_edge(base, shift, bk), full ? INFINITY : R * R);
+            const float lo_k = bk > 0 ? bin_edge(base, shift, bk - 1) : -1.f;
+            if ((shift != kShift0 || top != top0) && bo >= bk0) {
+                edge_o = edge_k;
+                upto_o = upto_k;
+            }
+            edge_o = fminf(edge_o, edge_k);
+
+            // ------------- scan B: gather every entry up to the Ndens-th bin,
+            // from the cells that meet its ball
+            if (!full) {
+                const float e2 = edge_k * 1.00001f + box * box * 1e-12f;
+                int keep_n = 0;
+                for (int c0 = 0; c0 < nc; c0 += 32) {
+                    const int j = c0 + lane;
+                    uint32_t ra = 0, ln = 0;
+                    bool keep = false;
+                    if (j < nc) {
+                        ra = cra[j];
+                        ln = cln[j];
+                        keep = cmd[j] <= e2;
+                    }
+                    const uint32_t bal = __ballot_sync(kAll, keep);
+                    __syncwarp();
+                    const int pos = keep_n + __popc(bal & lt);
+                    if (keep) {
+                        cra[pos] = ra;
+                        cln[pos] = ln;
+                    }
+                    keep_n += __popc(bal);
+                    __syncwarp();
+                }
+                nc = keep_n;
+                total = wq_prefix(cln, cpre, nc, lane);
+            }
+            int cnt = 0;
+            {
+                cand_acc += total;
+                wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t s, bool valid) {
+                    float d2 = INFINITY;
+                    if (valid) {
+                        float dx, dy, dz;
+                        if (full) {
+                            dx = wrapdiff(v.x, rqx, box, half);
+                            dy = wrapdiff(v.y, rqy, box, half);
+                            dz = wrapdiff(v.z, rqz, box, half);
+                        } else {
+                            dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
+                            dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
+                            dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
+                        }
+                        d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    }
+                    const bool keep = valid && d2 <= edge_k;
+                    const uint32_t bal = __ballot_sync(kAll, keep);
+                    const int pos = cnt + __popc(bal & lt);
+                    if (keep && pos < capq) {
+                        Ld[pos] = d2;
+                        Ls[pos] = s;
+                    }
+                    cnt += __popc(bal);
+                });
+            }
+            __syncwarp();
+            if (cnt != upto_k) {
+                // the two scans disagree: cannot happen with exact arithmetic
+                if (lane == 0) atomicOr(a.err, kErrKnnRetry);
+                continue;
+            }
+            // ------------- selection (the list is in Ld / Ls)
+            const float vk = list_kth<32>(true, Ld, cnt, cnt, lo_k, below_k, upto_k, k, kd, lane, kAll, lt);
+            unsigned long long wsum = 0;
+            const float rk = sqrtf(vk);
+            const float inv_h = vk > 0.f ? 2.f / rk : 0.f;
+            for (int e = lane; e < cnt; e += 32) {
+                const float v = Ld[e];
+                if (v < vk) {
+                    const float w = m4<float>(sqrtf(v) * inv_h);
+                    wsum += (unsigned long long)(w * 4294967296.0f + 0.5f);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kAll, wsum, o);
+            if (n_out > 0) {
+                if (upto_o <= kOC) {
+                    int no = 0;
+                    for (int e0 = 0; e0 < cnt; e0 += 32) {
+                        const int e = e0 + lane;
+                        float v = 0.f;
+                        uint32_t sv = 0;
+                        bool in = false;
+                        if (e < cnt) {
+                            v = Ld[e];
+                            sv = Ls[e];
+                            in = v <= edge_o;
+                        }
+                        const uint32_t bal = __ballot_sync(kAll, in);
+                        const int pos = no + __popc(bal & lt);
+                        if (in && pos < kOC) {
+                            od[pos] = v;
+                            os[pos] = sv;
+                        }
+                        no += __popc(bal);
+                    }
+                    __syncwarp();
+                    const int ng = min(no, kOC);
+                    if (lane < ng) {
+                        const float v = od[lane];
+                        const uint32_t se = os[lane];
+                        uint32_t oe = 0xffffffffu;
+                        int rank = 0;
+                        for (int f = 0; f < ng; ++f) {
+                            const float u = od[f];
+                            rank += u < v;
+                            if (u == v && f != lane) {
+                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
+                                rank += __float_as_uint(a.spos[os[f]].w) < oe;
+                            }
+                        }
+                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    }
+                } else {
+                    // many entries up to the n_out-th bin: rank in the list itself
+                    for (int e = lane; e < cnt; e += 32) {
+                        const float v = Ld[e];
+                        if (!(v <= edge_o)) continue;
+                        const uint32_t se = Ls[e];
+                        uint32_t oe = 0xffffffffu;
+                        int rank = 0;
+                        for (int f = 0; f < cnt; ++f) {
+                            const float u = Ld[f];
+                            if (u < v) {
+                                ++rank;
+                                continue;
+                            }
+                            if (u == v && f != e) {
+                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
+                                rank += __float_as_uint(a.spos[Ls[f]].w) < oe;
+                            }
+                        }
+                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    }
+                }
+            }
+            if (lane == 0) {
+                float dens;
+                if (vk > 0.f) {
+                    const float h = rk * 0.5f;
+                    dens = (float)(norm * ((float)wsum * 2.3283064365386963e-10f) / (h * h * h));
+                } else {
+                    dens = INFINITY;
+                }
+                a.dens_s[sq] = dens;
+                if (a.rk_s) a.rk_s[sq] = rk;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[kCntCand], cand_acc);
+        atomicAdd(&a.counters[kCntSearch], (unsigned long long)search_acc);
+        atomicAdd(&a.counters[kCntRetry], (unsigned long long)retry_acc);
+        atomicAdd(&a.counters[kCntWarps], (unsigned long long)warp_acc);
+    }
+}
+
+// ============================================ one query per warp, one scan
+// The warp-per-query search with a single scan: every particle with d^2
+// <= tau (tau = R^2 to begin with) goes into the warp's buffer; when the
+// buffer is nearly full, tau drops to an upper bound of the Ndens-th
+// distance of the particles seen so far (the upper edge of its bin) and the
+// buffer keeps only the entries up to it.  With a good first radius the
+// buffer never fills.  The search is certified when the buffer holds at
+// least Ndens entries after the whole ball of radius R was scanned; the
+// exact Ndens-th and n_out-th distances are then selected in the buffer.
+constexpr int kWbCap = 256;                 // buffer entries per warp
+
+struct WbSmem {
+    static constexpr size_t cra = 0;                                   // kWqCells range starts
+    static constexpr size_t cln = cra + kWqCells * 4;                  // kWqCells range lengths
+    static constexpr size_t cpre = cln + kWqCells * 4;                 // kWqCells + 1 prefix offsets
+    static constexpr size_t bd = (cpre + (kWqCells + 1) * 4 + 15) & ~size_t(15);   // kWbCap d^2
+    static constexpr size_t bs = bd + kWbCap * 4;                      // kWbCap sorted indices
+    static constexpr size_t hist = bs + kWbCap * 4;                    // kWqBins x 32 rows
+    static constexpr size_t kd = hist + kWqBins * 32 * 4;              // kKC values
+    static constexpr size_t od = kd + kKC * 4;                         // kOC values ...
+    static constexpr size_t os = od + kOC * 4;                         // ... and indices
+    static constexpr size_t total = (os + kOC * 4 + 15) & ~size_t(15);
+    static constexpr size_t cmd_scratch = 0;   // wq_cells writes min distances here (unused afterwards)
+};
+
+// Exact rank-th smallest of the warp's buffer entries in (lo, hi] (lo < the
+// entry values, below = the buffer entries <= lo): quarter-octave bins of
+// the bit pattern below hi, then 32 finer bins of the bin holding the entry
+// (or a lower window when it sits in the open lowest bin) until that bin
+// holds at most kKC entries, which are ranked.  Warp-uniform result.
+__device__ float wb_select(const float *bd, int cnt, int rank, float lo, float hi, int below, int *hist, float *kd,
+                           int lane, uint32_t lt)
+{
+    int top = (int)(__float_as_uint(hi) >> kShift0), shift = kShift0;
+    for (int guard = 0; guard < 24; ++guard) {
+        const int base = top - (kWqBins - 1);
+#pragma unroll 8
+        for (int b = 0; b < kWqBins; ++b) hist[b * 32 + lane] = 0;
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32) {
+            const float v = bd[e];
+            if (v > lo && v <= hi) hist[max((int)(__float_as_uint(v) >> shift) - base, 0) * 32 + lane] += 1;
+        }
+        __syncwarp();
+        int bk, bb, bu, tot;
+        wq_rows_find(hist, lane, rank - below, bk, bb, bu, tot);
+        if (bk < 0) return -1.f;   // fewer entries than rank: cannot happen for a certified buffer
+        const float nhi = fminf(bin_edge(base, shift, bk), hi);
+        const float nlo = bk > 0 ? fmaxf(bin_edge(base, shift, bk - 1), lo) : lo;
+        below += bb;
+        lo = nlo;
+        hi = nhi;
+        if (bu - bb <= kKC) break;
+        if (bk == 0 && base > 0) {
+            top -= kWqBins - 1;
+        } else if (shift > 0) {
+            const int ns = max(shift - 5, 0), d = shift - ns;
+            top = ((base + bk) << d) | ((1 << d) - 1);
+            shift = ns;
+        } else {
+            return hi;   // every entry of the bin has this one value
+        }
+    }
+    // rank the entries of (lo, hi]
+    int nk = 0;
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        float v = 0.f;
+        bool in = false;
+        if (e < cnt) {
+            v = bd[e];
+            in = v > lo && v <= hi;
+        }
+        const uint32_t bal = __ballot_sync(kAll, in);
+        const int pos = nk + __popc(bal & lt);
+        if (in && pos < kKC) kd[pos] = v;
+        nk += __popc(bal);
+    }
+    __syncwarp();
+    nk = min(nk, kKC);
+    float out = -1.f;
+    if (lane < nk) {
+        const float v = kd[lane];
+        int l0 = below, le = below;
+        for (int f = 0; f < nk; ++f) {
+            const float u = kd[f];
+            l0 += u < v;
+            le += u <= v;
+        }
+        if (l0 < rank && rank <= le) out = v;
+    }
+    out = cg_wmax(out);
+    __syncwarp();
+    return out;
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wb_kernel(CgDev a)
+{
+    using L = WbSmem;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    unsigned char *wb = smem_raw + L::total * wib;
+    uint32_t *cra = (uint32_t *)(wb + L::cra);
+    uint32_t *cln = (uint32_t *)(wb + L::cln);
+    uint32_t *cpre = (uint32_t *)(wb + L::cpre);
+    float *bd = (float *)(wb + L::bd);
+    uint32_t *bs = (uint32_t *)(wb + L::bs);
+    int *hist = (int *)(wb + L::hist);
+    float *kd = (float *)(wb + L::kd);
+    float *od = (float *)(wb + L::od);
+    uint32_t *os = (uint32_t *)(wb + L::os);
+    // wq_cells also records each cell's distance; it goes to the histogram
+    // rows, which are free while the cells are listed
+    float *cmd = (float *)hist;
+    static_assert(kWqCells * 4 <= kWqBins * 32 * 4, "cell distances fit in the histogram rows");
+    const int k = a.k;
+    const int n_out = a.nbr_s ? a.n_out : 0;
+    const int cpr = min(max(a.cpr, 1), 3);
+    unsigned long long cand_acc = 0;
+    uint32_t search_acc = 0, retry_acc = 0, warp_acc = 0;
+
+    for (;;) {
+        unsigned long long ch = 0;
+        if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
+        ch = __shfl_sync(kAll, ch, 0);
+        if ((int64_t)ch >= a.n_chunks) break;
+        ++warp_acc;
+        int64_t s_first, n_end, seg_base;
+        float box, half, inv_box, norm, plain_r;
+        const uint32_t *cellT;
+        int level_dense;
+        if constexpr (SEG) {
+            const SegDesc &sd = a.seg[seg_of_chunk(a.seg, a.B, (int64_t)ch)];
+            seg_base = sd.base;
+            n_end = sd.base + sd.n;
+            s_first = sd.base + ((int64_t)ch - sd.chunk0) * kWqChunk;
+            box = (float)sd.box;
+            half = (float)(0.5 * sd.box);
+            inv_box = (float)(1.0 / sd.box);
+            norm = (float)sd.norm;
+            cellT = a.cellT + sd.cell0;
+            level_dense = sd.level_dense;
+            plain_r = sd.plain_r;
+        } else {
+            seg_base = 0;
+            n_end = a.n;
+            s_first = (int64_t)ch * kWqChunk;
+            box = a.box;
+            half = a.half_box;
+            inv_box = a.inv_box;
+            norm = a.norm;
+            cellT = a.cellT;
+            level_dense = a.level_dense;
+            plain_r = a.plain_r;
+        }
+        const int nq = (int)min((int64_t)kWqChunk, n_end - s_first);
+        float R0 = a.chunk_r ? a.chunk_r[ch] : plain_r;
+        if (!(R0 > 0.f)) R0 = box * 1e-6f;
+        for (int qi = 0; qi < nq; ++qi) {
+            const int64_t sq = s_first + qi;
+            const float4 qv = a.spos[sq];
+            const float rqx = qv.x, rqy = qv.y, rqz = qv.z;
+            float R = R0;
+            int tries = 0;
+            bool failed = false, full = false;
+            float tau = 0.f;
+            int cnt = 0;
+            for (;;) {
+                ++search_acc;
+                full = 2.f * R >= half;
+                // frame: on an axis where the ball crosses a face, coordinates
+                // >= L/2 move by -L (exact); a whole-box scan takes each pair's
+                // own minimum image
+                const bool fx = !full && (rqx - R < 0.f || rqx + R >= box);
+                const bool fy = !full && (rqy - R < 0.f || rqy + R >= box);
+                const bool fz = !full && (rqz - R < 0.f || rqz + R >= box);
+                const float qx = (fx && rqx >= half) ? rqx - box : rqx;
+                const float qy = (fy && rqy >= half) ? rqy - box : rqy;
+                const float qz = (fz && rqz >= half) ? rqz - box : rqz;
+                int nc;
+                if (full) {
+                    if (lane == 0) {
+                        cra[0] = (uint32_t)seg_base;
+                        cln[0] = (uint32_t)(n_end - seg_base);
+                    }
+                    __syncwarp();
+                    nc = 1;
+                } else {
+                    int l = 1;
+                    const float cells = box * (float)cpr / R;   // 2^l <= cells: side >= R / cpr
+                    while (l < kMaxLevel && (float)(1 << (l + 1)) <= cells) ++l;
+                    for (;;) {
+                        nc = wq_cells(qx, qy, qz, R, box, inv_box, l, cellT, a.keys, level_dense, cra, cln, cmd, lane,
+                                      lt);
+                        if (nc >= 0 || l <= 1) break;
+                        --l;   // too many cells meet the ball: take coarser ones
+                    }
+                }
+                const uint32_t total = wq_prefix(cln, cpre, nc, lane);
+                tau = full ? INFINITY : R * R;
+                cnt = 0;
+                cand_acc += total;
+                wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t s, bool valid) {
+                    float d2 = INFINITY;
+                    if (valid) {
+                        float dx, dy, dz;
+                        if (full) {
+                            dx = wrapdiff(v.x, rqx, box, half);
+                            dy = wrapdiff(v.y, rqy, box, half);
+                            dz = wrapdiff(v.z, rqz, box, half);
+                        } else {
+                            dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
+                            dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
+                            dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
+                        }
+                        d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    }
+                    const bool keep = valid && d2 <= tau;
+                    const uint32_t bal = __ballot_sync(kAll, keep);
+                    const int pos = cnt + __popc(bal & lt);
+                    if (keep) {
+                        bd[pos] = d2;
+                        bs[pos] = s;
+                    }
+                    cnt += __popc(bal);
+                    if (cnt > kWbCap - 32) {
+                        // nearly full: tau drops to an upper bound of the k-th
+                        // distance seen so far and the buffer keeps what is below
+                        __syncwarp();
+                        float nt = -1.f;
+                        if (cnt >= k) {
+                            float hi = tau;
+                            if (!(hi < INFINITY)) {
+                                float mx = 0.f;
+                                for (int e = lane; e < cnt; e += 32) mx = fmaxf(mx, bd[e]);
+                                hi = cg_wmax(mx);
+                            }
+                            nt = wb_select(bd, cnt, k, -1.f, hi, 0, hist, kd, lane, lt);
+                        }
+                        if (!(nt >= 0.f)) nt = tau;
+                        int w = 0;
+                        for (int e0 = 0; e0 < cnt; e0 += 32) {
+                            const int e = e0 + lane;
+                            float vv = 0.f;
+                            uint32_t ss = 0;
+                            bool kk = false;
+                            if (e < cnt) {
+                                vv = bd[e];
+                                ss = bs[e];
+                                kk = vv <= nt;
+                            }
+                            const uint32_t bb = __ballot_sync(kAll, kk);
+                            __syncwarp();
+                            if (kk) {
+                                bd[w + __popc(bb & lt)] = vv;
+                                bs[w + __popc(bb & lt)] = ss;
+                            }
+                            w += __popc(bb);
+                            __syncwarp();
+                        }
+                        cnt = w;
+                        tau = nt;
+                        if (cnt > kWbCap - 32) {
+                            // more equal distances than the buffer holds
+                            if (lane == 0) atomicOr(a.err, kErrDegenerate);
+                            cnt = kWbCap - 32;
+                        }
+                    }
+                });
+                __syncwarp();
+                if (cnt >= k) break;
+                ++retry_acc;
+                if (++tries >= kCgTries || full) {
+                    if (lane == 0) atomicOr(a.err, kErrKnnRetry);
+                    failed = true;
+                    break;
+                }
+                R *= fminf(fmaxf(1.25f, 1.1f * cbrtf((float)k / (float)max(cnt, 1))), 8.f);
+            }
+            if (failed) continue;
+            // ------------- selection in the buffer
+            float hi = tau;
+            if (!(hi < INFINITY)) {
+                float m = 0.f;
+                for (int e = lane; e < cnt; e += 32) m = fmaxf(m, bd[e]);
+                hi = cg_wmax(m);
+            }
+            const float vk = wb_select(bd, cnt, k, -1.f, hi, 0, hist, kd, lane, lt);
+            unsigned long long wsum = 0;
+            const float rk = sqrtf(vk);
+            const float inv_h = vk > 0.f ? 2.f / rk : 0.f;
+            for (int e = lane; e < cnt; e += 32) {
+                const float v = bd[e];
+                if (v < vk) {
+                    const float w = m4<float>(sqrtf(v) * inv_h);
+                    wsum += (unsigned long long)(w * 4294967296.0f + 0.5f);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kAll, wsum, o);
+            if (n_out > 0) {
+                // the n_out-th distance, then the entries up to it, ranked by
+                // (d^2, original index)
+                const float vo = n_out == k ? vk : wb_select(bd, cnt, n_out, -1.f, vk, 0, hist, kd, lane, lt);
+                int no = 0;
+                for (int e0 = 0; e0 < cnt; e0 += 32) {
+                    const int e = e0 + lane;
+                    float v = 0.f;
+                    uint32_t sv = 0;
+                    bool in = false;
+                    if (e < cnt) {
+                        v = bd[e];
+                        sv = bs[e];
+                        in = v <= vo;
+                    }
+                    const uint32_t bal = __ballot_sync(kAll, in);
+                    const int pos = no + __popc(bal & lt);
+                    if (in && pos < kOC) {
+                        od[pos] = v;
+                        os[pos] = sv;
+                    }
+                    no += __popc(bal);
+                }
+                __syncwarp();
+                if (no <= kOC) {
+                    if (lane < no) {
+                        const float v = od[lane];
+                        const uint32_t se = os[lane];
+                        uint32_t oe = 0xffffffffu;
+                        int rank = 0;
+                        for (int f = 0; f < no; ++f) {
+                            const float u = od[f];
+                            rank += u < v;
+                            if (u == v && f != lane) {
+                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
+                                rank += __float_as_uint(a.spos[os[f]].w) < oe;
+                            }
+                        }
+                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    }
+                } else {
+                    // more than kOC entries up to the n_out-th: rank in the buffer
+                    for (int e = lane; e < cnt; e += 32) {
+                        const float v = bd[e];
+                        if (!(v <= vo)) continue;
+                        const uint32_t se = bs[e];
+                        uint32_t oe = 0xffffffffu;
+                        int rank = 0;
+                        for (int f = 0; f < cnt; ++f) {
+                            const float u = bd[f];
+                            if (u < v) {
+                                ++rank;
+                                continue;
+                            }
+                            if (u == v && f != e) {
+                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
+                                rank += __float_as_uint(a.spos[bs[f]].w) < oe;
+                            }
+                        }
+                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    }
+                }
+            }
+            if (lane == 0) {
+                float dens;
+                if (vk > 0.f) {
+                    const float h = rk * 0.5f;
+                    dens = (float)(norm * ((float)wsum * 2.3283064365386963e-10f) / (h * h * h));
+                } else {
+                    dens = INFINITY;
+                }
+                a.dens_s[sq] = dens;
+                if (a.rk_s) a.rk_s[sq] = rk;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[kCntCand], cand_acc);
+        atomicAdd(&a.counters[kCntSearch], (unsigned long long)search_acc);
+        atomicAdd(&a.counters[kCntRetry], (unsigned long long)retry_acc);
+        atomicAdd(&a.counters[kCntWarps], (unsigned long long)warp_acc);
+    }
+}
+
+template <bool SEG> int knn_wb_run(hop_ctx *c, const KnnArgs &ka, int cpr)
+{
+    CgDev d;
+    d.spos = (const float4 *)ka.spos;
+    d.keys = ka.keys;
+    d.cellT = ka.cellT;
+    d.level_dense = ka.level_dense;
+    d.n = ka.n;
+    d.n_chunks = SEG ? ka.n_chunks : (ka.n + kWqChunk - 1) / kWqChunk;
+    d.box = (float)ka.box;
+    d.inv_box = (float)(1.0 / ka.box);
+    d.half_box = (float)(0.5 * ka.box);
+    d.norm = (float)(ka.box * ka.box * ka.box / ((double)(ka.n_norm > 0 ? ka.n_norm : ka.n) * 3.14159265358979323846));
+    d.k = ka.k;
+    d.n_out = ka.n_out;
+    d.ld_out = ka.ld_out;
+    d.capq = kWbCap;
+    d.chunk_r = ka.chunk_r;
+    d.plain_r = ka.plain_r;
+    d.cpr = cpr;
+    d.seg = ka.seg;
+    d.B = ka.B;
+    d.nbr_s = ka.nbr_s;
+    d.dens_s = ka.dens_s;
+    d.rk_s = ka.rk_s;
+    d.counters = c->d_counters;
+    d.chunk_counter = c->d_counters + kCntNum;
+    d.err = c->d_err;
+    if (ka.k > kWbCap - 64) return ctx_fail(c, HOP_EINVAL, "n_dens too large for the one-scan buffer");
+    HOP_CUDA(c, cudaMemsetAsync(d.chunk_counter, 0, sizeof(unsigned long long), c->stream));
+    const int warps = kCgWarps;
+    const size_t smem = WbSmem::total * warps;
+    auto kern = knn_wb_kernel<SEG>;
+    HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
+    if (per_sm < 1) return ctx_fail(c, HOP_EINVAL, "kNN buffer does not fit in shared memory");
+    int64_t blocks = (int64_t)per_sm * c->num_sms;
+    const int64_t need = (d.n_chunks + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, warps * 32, smem, c->stream>>>(d);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
+template <bool SEG> int knn_wq_run(hop_ctx *c, const KnnArgs &ka, int cpr)
+{
+    CgDev d;
+    d.spos = (const float4 *)ka.spos;
+    d.keys = ka.keys;
+    d.cellT = ka.cellT;
+    d.level_dense = ka.level_dense;
+    d.n = ka.n;
+    d.n_chunks = SEG ? ka.n_chunks : (ka.n + kWqChunk - 1) / kWqChunk;
+    d.box = (float)ka.box;
+    d.inv_box = (float)(1.0 / ka.box);
+    d.half_box = (float)(0.5 * ka.box);
+    d.norm = (float)(ka.box * ka.box * ka.box / ((double)(ka.n_norm > 0 ? ka.n_norm : ka.n) * 3.14159265358979323846));
+    d.k = ka.k;
+    d.n_out = ka.n_out;
+    d.ld_out = ka.ld_out;
+    d.capq = ((ka.k + 32 + 7) / 8) * 8;
+    d.chunk_r = ka.chunk_r;
+    d.plain_r = ka.plain_r;
+    d.cpr = cpr;
+    d.seg = ka.seg;
+    d.B = ka.B;
+    d.nbr_s = ka.nbr_s;
+    d.dens_s = ka.dens_s;
+    d.rk_s = ka.rk_s;
+    d.counters = c->d_counters;
+    d.chunk_counter = c->d_counters + kCntNum;
+    d.err = c->d_err;
+    HOP_CUDA(c, cudaMemsetAsync(d.chunk_counter, 0, sizeof(unsigned long long), c->stream));
+    const size_t per_warp = WqSmem::total(d.capq);
+    const int warps = kCgWarps;
+    const size_t smem = per_warp * warps;
+    auto kern = knn_wq_kernel<SEG>;
+    HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
+    if (per_sm < 1) return ctx_fail(c, HOP_EINVAL, "kNN list does not fit in shared memory");
+    int64_t blocks = (int64_t)per_sm * c->num_sms;
+    const int64_t need = (d.n_chunks + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, warps * 32, smem, c->stream>>>(d);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
+
 template <int P, bool SEG> int knn_cg_run(hop_ctx *c, const KnnArgs &ka, int cpr)
 {
     constexpr int Q = 32 / P;
@@ -869,7 +1885,8 @@ int knn_cg_launch(hop_ctx *c, const KnnArgs &a, int qpw, int cpr)
     switch (qpw) {
     case 16: return a.seg ? knn_cg_run<2, true>(c, a, cpr) : knn_cg_run<2, false>(c, a, cpr);
     case 8: return a.seg ? knn_cg_run<4, true>(c, a, cpr) : knn_cg_run<4, false>(c, a, cpr);
-    case 4: return a.seg ? knn_cg_run<8, true>(c, a, cpr) : knn_cg_run<8, false>(c, a, cpr);
+    case 4: return a.seg ? knn_wb_run<true>(c, a, cpr) : knn_wb_run<false>(c, a, cpr);
+    case 2: return a.seg ? knn_wq_run<true>(c, a, cpr) : knn_wq_run<false>(c, a, cpr);
     default: return ctx_fail(c, HOP_EINVAL, "count-then-gather kNN takes 4, 8 or 16 queries per warp");
     }
 }

@@ -41,7 +41,8 @@ __global__ void root_flag_kernel(const uint32_t *__restrict__ chain, const uint6
 
 __global__ void root_list_kernel(const uint32_t *__restrict__ chain, const uint64_t *__restrict__ dkey,
                                  int64_t n, float d_o, float d_p, const uint32_t *__restrict__ cid,
-                                 uint64_t *__restrict__ ckey, uint8_t *__restrict__ own)
+                                 uint64_t *__restrict__ ckey, uint8_t *__restrict__ own, int64_t c_cap,
+                                 uint32_t *__restrict__ err)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -49,6 +50,10 @@ __global__ void root_list_kernel(const uint32_t *__restrict__ chain, const uint6
         const uint64_t k = dkey[i];
         if (!(key_dens(k) >= d_o)) continue;
         const uint32_t c = cid[i];
+        if (c >= (uint64_t)c_cap) {
+            atomicOr(err, kErrChainCap);
+            continue;
+        }
         ckey[c] = k;
         own[c] = key_dens(k) >= d_p ? 1 : 0;
     }
@@ -60,15 +65,16 @@ __global__ void edge_prep_kernel(const uint64_t *__restrict__ ekey, const double
                                  const uint32_t *__restrict__ cid, const uint64_t *__restrict__ dkey,
                                  float d_o, uint32_t *__restrict__ ea, uint32_t *__restrict__ eb,
                                  uint64_t *__restrict__ k1, uint32_t *__restrict__ v1,
-                                 uint32_t *__restrict__ err)
+                                 uint32_t *__restrict__ err, int64_t c_cap)
 {
     const int64_t m = mc.get();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t lo = (uint32_t)(ekey[e] >> 32), hi = (uint32_t)ekey[e];
-        if (lo >= (uint64_t)n || hi >= (uint64_t)n || chain[lo] != lo || chain[hi] != hi ||
-            !(key_dens(dkey[lo]) >= d_o) || !(key_dens(dkey[hi]) >= d_o) || lo == hi) {
-            atomicOr(err, kErrBadIndex);
+        const bool bad = lo >= (uint64_t)n || hi >= (uint64_t)n || chain[lo] != lo || chain[hi] != hi ||
+                         !(key_dens(dkey[lo]) >= d_o) || !(key_dens(dkey[hi]) >= d_o) || lo == hi;
+        if (bad || cid[lo] >= (uint64_t)c_cap || cid[hi] >= (uint64_t)c_cap) {
+            atomicOr(err, bad ? kErrBadIndex : kErrChainCap);
             ea[e] = eb[e] = 0;
             k1[e] = 0;
             v1[e] = (uint32_t)e;
@@ -356,12 +362,13 @@ int merge_groups(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, int64_
     void *tmp = base + o_tmp;
 
     HOP_CUDA(c, cudaMemsetAsync(own, 0, Cp, c->stream));
-    root_list_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, d_p, cid, ckey, own);
+    root_list_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, d_p, cid, ckey, own, Cp,
+                                                            d_merr);
     HOP_LAUNCH(c);
     // M3: strict order
     if (m > 0) {
         edge_prep_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(edge_key, edge_sum, DevCount{m, nullptr}, n, chain, cid,
-                                                               dkey, d_o, ea, eb, k1, v1, d_merr);
+                                                               dkey, d_o, ea, eb, k1, v1, d_merr, Cp);
         HOP_LAUNCH(c);
         rc = radix_sort_u64(c, k1, k1b, v1, v1b, m, 0, 64, tmp);
         if (rc) return rc;
@@ -483,7 +490,8 @@ int boruvka_round(hop_ctx *c, void *p)
 
 int merge_groups_graph(hop_ctx *c, const MergeGraphArgs &a)
 {
-    const int64_t n = a.n, Cmax = std::max<int64_t>(n, 1), mmax = std::max<int64_t>(a.m.max, 1);
+    const int64_t n = a.n, mmax = std::max<int64_t>(a.m.max, 1);
+    const int64_t Cmax = std::max<int64_t>(a.c_cap > 0 && a.c_cap < n ? a.c_cap : n, 1);
     uint32_t *d_C = a.counts, *d_G = a.counts + 1, *d_changed = a.counts + 2;
     uint32_t *d_round1 = a.counts + 3, *d_round2 = a.counts + 4;
     const DevCount C{Cmax, d_C}, G{Cmax, d_G};
@@ -523,11 +531,12 @@ int merge_groups_graph(hop_ctx *c, const MergeGraphArgs &a)
     HOP_LAUNCH(c);
     int rc = scan_exclusive_u32(c, cid, cid, n, d_C);
     if (rc) return rc;
-    root_list_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(a.chain, a.dkey, n, a.d_o, a.d_p, cid, ckey, own);
+    root_list_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(a.chain, a.dkey, n, a.d_o, a.d_p, cid, ckey, own,
+                                                            Cmax, c->d_err);
     HOP_LAUNCH(c);
     // M3: strict edge order
     edge_prep_kernel<<<grid_for(c, mmax), 256, 0, c->stream>>>(a.edge_key, a.edge_sum, a.m, n, a.chain, cid,
-                                                              a.dkey, a.d_o, ea, eb, k1, v1, c->d_err);
+                                                              a.dkey, a.d_o, ea, eb, k1, v1, c->d_err, Cmax);
     HOP_LAUNCH(c);
     rc = radix_sort_u64_dev(c, k1, k1b, v1, v1b, a.m, 0, 64, tmp);
     if (rc) return rc;

@@ -125,50 +125,94 @@ __global__ void radix_hist_kernel(const uint64_t *__restrict__ keys, DevCount nc
         counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
 }
 
-// Stable scatter: items are taken in input order (round-major, then thread),
-// ranked within their warp with match/popc, then across warps per digit.
-__global__ void radix_scatter_kernel(const uint64_t *__restrict__ keys_in,
-                                     const uint32_t *__restrict__ vals_in,
-                                     uint64_t *__restrict__ keys_out,
-                                     uint32_t *__restrict__ vals_out, DevCount nc, int shift,
-                                     int64_t nblocks, const uint32_t *__restrict__ offsets)
+// Stable scatter through a tile-local sort.  A block takes 4096 items: warp
+// w ranks its 512 (16 rounds of 32 consecutive items, input order) per digit
+// with match/popc and its own digit counters; a scan over (digit, warp)
+// gives each item its position in the tile sorted by digit; the tile is
+// rebuilt in shared memory in that order and written out in order, so each
+// digit's run goes to consecutive global addresses.
+constexpr int kLsSmem = kSortWarps * 256 * 4 + 256 * 4 * 2 + kSortTile * 12;
+
+__global__ void __launch_bounds__(kSortThreads, 2) radix_local_scatter_kernel(
+    const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint64_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, DevCount nc, int shift, int64_t nblocks, const uint32_t *__restrict__ offsets)
 {
+    extern __shared__ __align__(16) unsigned char ls_raw[];
+    uint32_t *wcnt = (uint32_t *)ls_raw;                       // [warp][digit]
+    uint32_t *lstart = wcnt + kSortWarps * 256;                // digit -> first tile position
+    uint32_t *gbase = lstart + 256;                            // digit -> global position of tile position 0
+    uint64_t *skey = (uint64_t *)(gbase + 256);
+    uint32_t *sval = (uint32_t *)(skey + kSortTile);
     const int64_t n = nc.get();
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[kSortWarps][256];
     const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x)
-        base[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    const uint32_t lt = lanemask_lt();
     const int64_t tile = (int64_t)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortItems; ++r) {
-        for (int t = threadIdx.x; t < kSortWarps * 256; t += blockDim.x) (&wcnt[0][0])[t] = 0;
-        __syncthreads();
-        const int64_t i = tile + (int64_t)r * kSortThreads + threadIdx.x;
-        const bool valid = i < n;
-        uint64_t key = valid ? keys_in[i] : 0ull;
-        uint32_t val = valid ? vals_in[i] : 0u;
-        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lanemask_lt());
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < 256; dd += blockDim.x) {
-            uint32_t run = base[dd];
+    for (int t = threadIdx.x; t < kSortWarps * 256; t += kSortThreads) wcnt[t] = 0;
+    __syncthreads();
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems], rnk[kSortItems];
+    uint32_t *mycnt = wcnt + warp * 256;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) {
-                uint32_t c = wcnt[w][dd];
-                wcnt[w][dd] = run;
-                run += c;
-            }
-            base[dd] = run;
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = tile + (int64_t)warp * (32 * kSortItems) + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? keys_in[i] : 0ull;
+        val[r] = valid ? vals_in[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = tile + (int64_t)warp * (32 * kSortItems) + r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t prior = 0;
+        if (valid && lane == leader) {
+            prior = mycnt[d];
+            mycnt[d] = prior + __popc(peers);
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t dst = wcnt[warp][d] + rank;
-            keys_out[dst] = key;
-            vals_out[dst] = val;
+        prior = __shfl_sync(0xffffffffu, prior, leader);
+        rnk[r] = prior + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // digit d = threadIdx.x: the runs of the 8 warps, then the tile scan
+        const uint32_t d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = wcnt[w * 256 + d];
+            wcnt[w * 256 + d] = run;
+            run += c;
         }
-        __syncthreads();
+        __shared__ uint32_t sw[33];
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(run, sw, &tot);
+        lstart[d] = ex;
+        gbase[d] = offsets[(int64_t)d * nblocks + blockIdx.x] - ex;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) wcnt[w * 256 + d] += ex;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = tile + (int64_t)warp * (32 * kSortItems) + r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (uint32_t)((key[r] >> shift) & 255u);
+            const uint32_t p = mycnt[d] + rnk[r];
+            skey[p] = key[r];
+            sval[p] = val[r];
+        }
+    }
+    __syncthreads();
+    const int64_t m = n - tile < kSortTile ? n - tile : kSortTile;
+    for (int p = threadIdx.x; p < m; p += kSortThreads) {
+        const uint64_t k = skey[p];
+        const uint32_t d = (uint32_t)((k >> shift) & 255u);
+        const uint32_t dst = gbase[d] + (uint32_t)p;
+        keys_out[dst] = k;
+        vals_out[dst] = sval[p];
     }
 }
 
@@ -257,12 +301,13 @@ int radix_sort_u64_dev(hop_ctx *c, uint64_t *&keys, uint64_t *&keys_alt, uint32_
     if (n.max <= 0) return HOP_OK;
     const int64_t nb = (n.max + kSortTile - 1) / kSortTile;
     uint32_t *counts = (uint32_t *)scratch;
+    HOP_CUDA(c, cudaFuncSetAttribute(radix_local_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLsSmem));
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         radix_hist_kernel<<<(unsigned)nb, kSortThreads, 0, c->stream>>>(keys, n, shift, nb, counts);
         HOP_LAUNCH(c);
         int rc = scan_exclusive_u32(c, counts, counts, 256 * nb, nullptr);
         if (rc) return rc;
-        radix_scatter_kernel<<<(unsigned)nb, kSortThreads, 0, c->stream>>>(
+        radix_local_scatter_kernel<<<(unsigned)nb, kSortThreads, kLsSmem, c->stream>>>(
             keys, vals, keys_alt, vals_alt, n, shift, nb, counts);
         HOP_LAUNCH(c);
         uint64_t *tk = keys; keys = keys_alt; keys_alt = tk;

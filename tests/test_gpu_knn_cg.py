@@ -1,5 +1,6 @@
-"""The count-then-gather kNN kernel (float32, 4, 8 or 16 queries per warp)
-against the single-scan kernel with a candidate buffer: both are exact, so
+"""The count-then-gather kNN kernels (float32: one warp per query with one
+scan at 4 queries per warp, with two scans at 2, grouped queries at 8 and
+16) against the single-scan kernel with a candidate buffer: all are exact, so
 neighbour lists, densities, r_k and group ids must be bit-identical, on
 clustered, tied, tiny, wrapped and batched inputs, with every first-radius
 policy and the paper's own list lengths.  The default tuning runs the
@@ -63,7 +64,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("qpw", [4, 8, 16])
+@pytest.mark.parametrize("qpw", [2, 4, 8, 16])
 @pytest.mark.parametrize("case", list(CASES))
 def test_count_gather_equals_single_scan(hop, case, qpw):
     pos = CASES[case]()
@@ -74,15 +75,16 @@ def test_count_gather_equals_single_scan(hop, case, qpw):
 
 
 @pytest.mark.parametrize("case", ["clump_at_kth", "lattice16"])
-def test_count_gather_against_oracle(hop, case):
+@pytest.mark.parametrize("qpw", [2, 4, 8])
+def test_count_gather_against_oracle(hop, case, qpw):
     pos = CASES[case]()
     n = len(pos)
-    nbr, dens, _ = _density(hop, pos, 8, 0, 16)
+    nbr, dens, _ = _density(hop, pos, qpw, 0, 16)
     _, d2_o = check_knn_rows(pos, nbr.cpu().numpy(), np.arange(n), 64, name=case)
     check_density(dens.cpu().numpy(), d2_o, n, name=case)
 
 
-@pytest.mark.parametrize("qpw", [4, 8, 16])
+@pytest.mark.parametrize("qpw", [2, 4, 8, 16])
 def test_count_gather_full_list_and_paper_defaults(hop, qpw):
     pos = synth.nfw_box(30001, 13, halo_frac=0.7)[0]
     # all 64 entries of every list
@@ -97,10 +99,11 @@ def test_count_gather_full_list_and_paper_defaults(hop, qpw):
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("qpw", [4, 8])
 @pytest.mark.parametrize("mode", [hopgpu.HOP_RADIUS_PLAIN, hopgpu.HOP_RADIUS_COUNT])
-def test_count_gather_radius_policies(hop, mode):
+def test_count_gather_radius_policies(hop, mode, qpw):
     pos = synth.nfw_box(50000, 17)[0]
-    a = _density(hop, pos, 8, 0, 16, radius_mode=mode)
+    a = _density(hop, pos, qpw, 0, 16, radius_mode=mode)
     b = _density(hop, pos, 8, 4, 16, radius_mode=hopgpu.HOP_RADIUS_PLAIN)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
@@ -116,12 +119,15 @@ def test_count_gather_batched_subvolumes(hop):
         boxes.append(L)
     pos = np.concatenate(parts)
     out = {}
-    for buf in (0, 4):
-        hop.apply_tuning(8, 1, buf)
+    for qpw, buf in ((8, 4), (4, 0), (8, 0), (16, 0)):
+        hop.apply_tuning(qpw, 2, buf)
         try:
-            out[buf] = hop.hop_run_batch(_dev(pos), off, boxes, hopgpu.default_params(), ld_nbr=16, eager=True)
+            out[(qpw, buf)] = hop.hop_run_batch(_dev(pos), off, boxes, hopgpu.default_params(), ld_nbr=16,
+                                                eager=True)
         finally:
             hop.apply_tuning(8, 1, 0)
-    for key in ("dens", "group", "nbr"):
-        assert torch.equal(out[0][key], out[4][key]), key
-    assert np.array_equal(out[0]["n_groups"], out[4]["n_groups"])
+    ref = out[(8, 4)]
+    for t, o in out.items():
+        for key in ("dens", "group", "nbr"):
+            assert torch.equal(ref[key], o[key]), (t, key)
+        assert np.array_equal(ref["n_groups"], o["n_groups"])
