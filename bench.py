@@ -281,17 +281,29 @@ def timed(fn, steps, dist, hop):
     return ms, stats
 
 
+def knn_kernel_name(t):
+    """The kNN kernel a (queries per warp, cells per radius, buffer factor)
+    tuning runs (float32 positions)."""
+    qpw, _, buf = t
+    if qpw == 32:
+        return "knn32_kernel"
+    if buf:
+        return "knn_kernel (single scan)"
+    return "knn_wq_kernel (one warp per query)" if qpw == 4 else "knn_cg_kernel (grouped queries)"
+
+
 def stage(st):
     keys = ("ms_sort", "ms_radius", "ms_knn", "ms_link", "ms_boundaries", "ms_merge", "ms_total")
     return {k[3:]: round(statistics.median(s[k] for s in st), 3) for k in keys}
 
 
-CANDS = {"learned": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (4, 1, 3), (32, 1, 0), (32, 1, 3)],
-         "count": [(4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 2, 0), (32, 1, 3)],
-         "plain": [(4, 1, 0), (8, 1, 0), (32, 1, 0), (32, 1, 3)]}
-# boxes of 2^29 particles or more run through hop_run (the batched pass sizes
-# its merge arrays by the particle count) with these fixed tunings
-FIXED = {"learned": (4, 1, 0), "count": (4, 1, 0), "plain": (32, 1, 3)}
+# (queries per warp, cells per radius, buffer factor): 4 queries per warp runs
+# the one-warp-per-query kernel, 8 and 16 the grouped count-then-gather
+# kernel, 32 one query per lane; a buffer factor selects the single-scan
+# kernel with that candidate buffer
+CANDS = {"learned": [(4, 2, 0), (4, 1, 0), (4, 3, 0), (8, 1, 0), (8, 2, 0), (16, 1, 0), (4, 1, 3), (32, 1, 3)],
+         "count": [(4, 2, 0), (4, 1, 0), (8, 1, 0), (16, 1, 0), (4, 1, 3), (32, 1, 3)],
+         "plain": [(4, 2, 0), (8, 2, 0), (32, 1, 0), (32, 1, 3)]}
 
 
 def batch_section(hop, args, dist):
@@ -384,14 +396,10 @@ def run_gb300(args):
            "dens": torch.empty(n, dtype=torch.float32, device="cuda")}
     params = {"learned": default_params(radius_mode=2), "plain": default_params(radius_mode=0),
               "count": default_params(radius_mode=1)}
-    single = n >= (1 << 29)
     # the autotuner (graph replays, untimed) picks each policy's tuning;
     # output does not depend on it
     tuned = {}
     for name in ("learned", "count", "plain"):
-        if single:
-            tuned[name] = FIXED[name]
-            continue
         cs = CANDS[name][:1] if args.no_tune else CANDS[name]
         best, tr = hop.hop_autotune(dpos, off, boxes, params[name], cs, reps=1)
         tuned[name] = tuple(cs[best])
@@ -400,8 +408,6 @@ def run_gb300(args):
         hop.apply_tuning(*tuned[name])
 
     def call(name, pos_in, o):
-        if single:
-            return int(hop.hop_run(pos_in, params[name], out=o)["n_groups"])
         return int(hop.hop_run_batch(pos_in, off, boxes, params[name], out=o)["n_groups"][0])
 
     def step(name):
@@ -412,12 +418,8 @@ def run_gb300(args):
     ref = {}
     for name in ("plain", "learned", "count"):
         configure(name)
-        if single:
-            r = hop.hop_run(dpos, params[name], ld_nbr=N_HOP)
-            ng = int(r["n_groups"])
-        else:
-            r = hop.hop_run_batch(dpos, off, boxes, params[name], ld_nbr=N_HOP)
-            ng = int(r["n_groups"][0])
+        r = hop.hop_run_batch(dpos, off, boxes, params[name], ld_nbr=N_HOP)
+        ng = int(r["n_groups"][0])
         ref[name] = (r["group"], r["dens"], r["nbr"], ng)
         del r
     same = all(torch.equal(ref["plain"][0], ref[k][0]) and torch.equal(ref["plain"][1], ref[k][1])
@@ -493,13 +495,10 @@ def run_gb300(args):
     # the single-volume call (hop_run, host round trips between stages) on
     # the same box and tuning, for comparison
     configure("learned")
-    if single:
-        ms_single = results["learned"][0]
-    else:
-        for _ in range(max(1, args.warmup - 1)):
-            hop.hop_run(dpos, params["learned"], out=out)
-        ms_single, _ = timed(lambda: hop.hop_run(dpos, params["learned"], out=out), args.steps, dist, hop)
-        ms_single /= args.steps
+    for _ in range(max(1, args.warmup - 1)):
+        hop.hop_run(dpos, params["learned"], out=out)
+    ms_single, _ = timed(lambda: hop.hop_run(dpos, params["learned"], out=out), args.steps, dist, hop)
+    ms_single /= args.steps
 
     # end to end through the same C-ABI call with host (pinned) buffers
     hpos = torch.from_numpy(pos).pin_memory()
@@ -549,8 +548,7 @@ def run_gb300(args):
         "data": "synthetic",
         "config": {"workload": wl, "n_particles": n, "n_dens": N_DENS, "n_hop": N_HOP,
                    "n_merge": N_MERGE, "deltas": list(DELTAS), "radius": "learned",
-                   "path": ("hop_run (single call; 2^29 particles or more)" if single else
-                            "hop_run_batch (one subvolume), graph-captured pass"),
+                   "path": "hop_run_batch (one subvolume), graph-captured pass",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs (12 B/particle, %.2f GB) larger than L2; no flush" % (n * 12 / 1e9),
                    "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1], "buf_factor": v[2]}
@@ -572,7 +570,7 @@ def run_gb300(args):
         "ablation": ("plain: the first radius is the mean-density Ndens-th-neighbour distance, "
                      "then certified stencil expansion; count: the closed-form radius from the 27 "
                      "stencil counts, the non-learned policy closest to the network"),
-        "roofline": {"kernel": "knn_kernel<float,P,SEG> (kNN + M4 density)", "bound": "alu",
+        "roofline": {"kernel": knn_kernel_name(tuned["learned"]) + " (kNN + M4 density)", "bound": "alu",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": (tpp * n if tpp else None),
                      "traffic_basis": tsrc,

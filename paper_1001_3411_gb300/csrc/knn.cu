@@ -1120,7 +1120,7 @@ int knn_launch(hop_ctx *c, const KnnArgs &a, bool f64, int qpw, int cpr)
     if (qpw == 32 && !f64) return knn32_launch(c, a, cpr);   // one query per lane
     // float32 with 4, 8 or 16 queries per warp: the count-then-gather kernel,
     // unless a candidate-buffer factor was set (the single-scan kernel below)
-    if (!f64 && c->capf == 0 && (qpw == 2 || qpw == 4 || qpw == 8 || qpw == 16)) return knn_cg_launch(c, a, qpw, cpr);
+    if (!f64 && c->capf == 0 && (qpw == 4 || qpw == 8 || qpw == 16)) return knn_cg_launch(c, a, qpw, cpr);
     if (a.seg) {
         // batched passes: float32 positions, 4, 8, 16 or 32 queries per warp
         if (f64) return ctx_fail(c, HOP_EINVAL, "batched passes take float32 positions");

@@ -1343,440 +1343,6 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
     }
 }
 
-// ============================================ one query per warp, one scan
-// The warp-per-query search with a single scan: every particle with d^2
-// <= tau (tau = R^2 to begin with) goes into the warp's buffer; when the
-// buffer is nearly full, tau drops to an upper bound of the Ndens-th
-// distance of the particles seen so far (the upper edge of its bin) and the
-// buffer keeps only the entries up to it.  With a good first radius the
-// buffer never fills.  The search is certified when the buffer holds at
-// least Ndens entries after the whole ball of radius R was scanned; the
-// exact Ndens-th and n_out-th distances are then selected in the buffer.
-constexpr int kWbCap = 256;                 // buffer entries per warp
-
-struct WbSmem {
-    static constexpr size_t cra = 0;                                   // kWqCells range starts
-    static constexpr size_t cln = cra + kWqCells * 4;                  // kWqCells range lengths
-    static constexpr size_t cpre = cln + kWqCells * 4;                 // kWqCells + 1 prefix offsets
-    static constexpr size_t bd = (cpre + (kWqCells + 1) * 4 + 15) & ~size_t(15);   // kWbCap d^2
-    static constexpr size_t bs = bd + kWbCap * 4;                      // kWbCap sorted indices
-    static constexpr size_t hist = bs + kWbCap * 4;                    // kWqBins x 32 rows
-    static constexpr size_t kd = hist + kWqBins * 32 * 4;              // kKC values
-    static constexpr size_t od = kd + kKC * 4;                         // kOC values ...
-    static constexpr size_t os = od + kOC * 4;                         // ... and indices
-    static constexpr size_t total = (os + kOC * 4 + 15) & ~size_t(15);
-    static constexpr size_t cmd_scratch = 0;   // wq_cells writes min distances here (unused afterwards)
-};
-
-// Exact rank-th smallest of the warp's buffer entries in (lo, hi] (lo < the
-// entry values, below = the buffer entries <= lo): quarter-octave bins of
-// the bit pattern below hi, then 32 finer bins of the bin holding the entry
-// (or a lower window when it sits in the open lowest bin) until that bin
-// holds at most kKC entries, which are ranked.  Warp-uniform result.
-__device__ float wb_select(const float *bd, int cnt, int rank, float lo, float hi, int below, int *hist, float *kd,
-                           int lane, uint32_t lt)
-{
-    int top = (int)(__float_as_uint(hi) >> kShift0), shift = kShift0;
-    for (int guard = 0; guard < 24; ++guard) {
-        const int base = top - (kWqBins - 1);
-#pragma unroll 8
-        for (int b = 0; b < kWqBins; ++b) hist[b * 32 + lane] = 0;
-        __syncwarp();
-        for (int e = lane; e < cnt; e += 32) {
-            const float v = bd[e];
-            if (v > lo && v <= hi) hist[max((int)(__float_as_uint(v) >> shift) - base, 0) * 32 + lane] += 1;
-        }
-        __syncwarp();
-        int bk, bb, bu, tot;
-        wq_rows_find(hist, lane, rank - below, bk, bb, bu, tot);
-        if (bk < 0) return -1.f;   // fewer entries than rank: cannot happen for a certified buffer
-        const float nhi = fminf(bin_edge(base, shift, bk), hi);
-        const float nlo = bk > 0 ? fmaxf(bin_edge(base, shift, bk - 1), lo) : lo;
-        below += bb;
-        lo = nlo;
-        hi = nhi;
-        if (bu - bb <= kKC) break;
-        if (bk == 0 && base > 0) {
-            top -= kWqBins - 1;
-        } else if (shift > 0) {
-            const int ns = max(shift - 5, 0), d = shift - ns;
-            top = ((base + bk) << d) | ((1 << d) - 1);
-            shift = ns;
-        } else {
-            return hi;   // every entry of the bin has this one value
-        }
-    }
-    // rank the entries of (lo, hi]
-    int nk = 0;
-    for (int e0 = 0; e0 < cnt; e0 += 32) {
-        const int e = e0 + lane;
-        float v = 0.f;
-        bool in = false;
-        if (e < cnt) {
-            v = bd[e];
-            in = v > lo && v <= hi;
-        }
-        const uint32_t bal = __ballot_sync(kAll, in);
-        const int pos = nk + __popc(bal & lt);
-        if (in && pos < kKC) kd[pos] = v;
-        nk += __popc(bal);
-    }
-    __syncwarp();
-    nk = min(nk, kKC);
-    float out = -1.f;
-    if (lane < nk) {
-        const float v = kd[lane];
-        int l0 = below, le = below;
-        for (int f = 0; f < nk; ++f) {
-            const float u = kd[f];
-            l0 += u < v;
-            le += u <= v;
-        }
-        if (l0 < rank && rank <= le) out = v;
-    }
-    out = cg_wmax(out);
-    __syncwarp();
-    return out;
-}
-
-template <bool SEG>
-__global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wb_kernel(CgDev a)
-{
-    using L = WbSmem;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    unsigned char *wb = smem_raw + L::total * wib;
-    uint32_t *cra = (uint32_t *)(wb + L::cra);
-    uint32_t *cln = (uint32_t *)(wb + L::cln);
-    uint32_t *cpre = (uint32_t *)(wb + L::cpre);
-    float *bd = (float *)(wb + L::bd);
-    uint32_t *bs = (uint32_t *)(wb + L::bs);
-    int *hist = (int *)(wb + L::hist);
-    float *kd = (float *)(wb + L::kd);
-    float *od = (float *)(wb + L::od);
-    uint32_t *os = (uint32_t *)(wb + L::os);
-    // wq_cells also records each cell's distance; it goes to the histogram
-    // rows, which are free while the cells are listed
-    float *cmd = (float *)hist;
-    static_assert(kWqCells * 4 <= kWqBins * 32 * 4, "cell distances fit in the histogram rows");
-    const int k = a.k;
-    const int n_out = a.nbr_s ? a.n_out : 0;
-    const int cpr = min(max(a.cpr, 1), 3);
-    unsigned long long cand_acc = 0;
-    uint32_t search_acc = 0, retry_acc = 0, warp_acc = 0;
-
-    for (;;) {
-        unsigned long long ch = 0;
-        if (lane == 0) ch = atomicAdd(a.chunk_counter, 1ull);
-        ch = __shfl_sync(kAll, ch, 0);
-        if ((int64_t)ch >= a.n_chunks) break;
-        ++warp_acc;
-        int64_t s_first, n_end, seg_base;
-        float box, half, inv_box, norm, plain_r;
-        const uint32_t *cellT;
-        int level_dense;
-        if constexpr (SEG) {
-            const SegDesc &sd = a.seg[seg_of_chunk(a.seg, a.B, (int64_t)ch)];
-            seg_base = sd.base;
-            n_end = sd.base + sd.n;
-            s_first = sd.base + ((int64_t)ch - sd.chunk0) * kWqChunk;
-            box = (float)sd.box;
-            half = (float)(0.5 * sd.box);
-            inv_box = (float)(1.0 / sd.box);
-            norm = (float)sd.norm;
-            cellT = a.cellT + sd.cell0;
-            level_dense = sd.level_dense;
-            plain_r = sd.plain_r;
-        } else {
-            seg_base = 0;
-            n_end = a.n;
-            s_first = (int64_t)ch * kWqChunk;
-            box = a.box;
-            half = a.half_box;
-            inv_box = a.inv_box;
-            norm = a.norm;
-            cellT = a.cellT;
-            level_dense = a.level_dense;
-            plain_r = a.plain_r;
-        }
-        const int nq = (int)min((int64_t)kWqChunk, n_end - s_first);
-        float R0 = a.chunk_r ? a.chunk_r[ch] : plain_r;
-        if (!(R0 > 0.f)) R0 = box * 1e-6f;
-        for (int qi = 0; qi < nq; ++qi) {
-            const int64_t sq = s_first + qi;
-            const float4 qv = a.spos[sq];
-            const float rqx = qv.x, rqy = qv.y, rqz = qv.z;
-            float R = R0;
-            int tries = 0;
-            bool failed = false, full = false;
-            float tau = 0.f;
-            int cnt = 0;
-            for (;;) {
-                ++search_acc;
-                full = 2.f * R >= half;
-                // frame: on an axis where the ball crosses a face, coordinates
-                // >= L/2 move by -L (exact); a whole-box scan takes each pair's
-                // own minimum image
-                const bool fx = !full && (rqx - R < 0.f || rqx + R >= box);
-                const bool fy = !full && (rqy - R < 0.f || rqy + R >= box);
-                const bool fz = !full && (rqz - R < 0.f || rqz + R >= box);
-                const float qx = (fx && rqx >= half) ? rqx - box : rqx;
-                const float qy = (fy && rqy >= half) ? rqy - box : rqy;
-                const float qz = (fz && rqz >= half) ? rqz - box : rqz;
-                int nc;
-                if (full) {
-                    if (lane == 0) {
-                        cra[0] = (uint32_t)seg_base;
-                        cln[0] = (uint32_t)(n_end - seg_base);
-                    }
-                    __syncwarp();
-                    nc = 1;
-                } else {
-                    int l = 1;
-                    const float cells = box * (float)cpr / R;   // 2^l <= cells: side >= R / cpr
-                    while (l < kMaxLevel && (float)(1 << (l + 1)) <= cells) ++l;
-                    for (;;) {
-                        nc = wq_cells(qx, qy, qz, R, box, inv_box, l, cellT, a.keys, level_dense, cra, cln, cmd, lane,
-                                      lt);
-                        if (nc >= 0 || l <= 1) break;
-                        --l;   // too many cells meet the ball: take coarser ones
-                    }
-                }
-                const uint32_t total = wq_prefix(cln, cpre, nc, lane);
-                tau = full ? INFINITY : R * R;
-                cnt = 0;
-                cand_acc += total;
-                wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t s, bool valid) {
-                    float d2 = INFINITY;
-                    if (valid) {
-                        float dx, dy, dz;
-                        if (full) {
-                            dx = wrapdiff(v.x, rqx, box, half);
-                            dy = wrapdiff(v.y, rqy, box, half);
-                            dz = wrapdiff(v.z, rqz, box, half);
-                        } else {
-                            dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
-                            dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
-                            dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
-                        }
-                        d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    }
-                    const bool keep = valid && d2 <= tau;
-                    const uint32_t bal = __ballot_sync(kAll, keep);
-                    const int pos = cnt + __popc(bal & lt);
-                    if (keep) {
-                        bd[pos] = d2;
-                        bs[pos] = s;
-                    }
-                    cnt += __popc(bal);
-                    if (cnt > kWbCap - 32) {
-                        // nearly full: tau drops to an upper bound of the k-th
-                        // distance seen so far and the buffer keeps what is below
-                        __syncwarp();
-                        float nt = -1.f;
-                        if (cnt >= k) {
-                            float hi = tau;
-                            if (!(hi < INFINITY)) {
-                                float mx = 0.f;
-                                for (int e = lane; e < cnt; e += 32) mx = fmaxf(mx, bd[e]);
-                                hi = cg_wmax(mx);
-                            }
-                            nt = wb_select(bd, cnt, k, -1.f, hi, 0, hist, kd, lane, lt);
-                        }
-                        if (!(nt >= 0.f)) nt = tau;
-                        int w = 0;
-                        for (int e0 = 0; e0 < cnt; e0 += 32) {
-                            const int e = e0 + lane;
-                            float vv = 0.f;
-                            uint32_t ss = 0;
-                            bool kk = false;
-                            if (e < cnt) {
-                                vv = bd[e];
-                                ss = bs[e];
-                                kk = vv <= nt;
-                            }
-                            const uint32_t bb = __ballot_sync(kAll, kk);
-                            __syncwarp();
-                            if (kk) {
-                                bd[w + __popc(bb & lt)] = vv;
-                                bs[w + __popc(bb & lt)] = ss;
-                            }
-                            w += __popc(bb);
-                            __syncwarp();
-                        }
-                        cnt = w;
-                        tau = nt;
-                        if (cnt > kWbCap - 32) {
-                            // more equal distances than the buffer holds
-                            if (lane == 0) atomicOr(a.err, kErrDegenerate);
-                            cnt = kWbCap - 32;
-                        }
-                    }
-                });
-                __syncwarp();
-                if (cnt >= k) break;
-                ++retry_acc;
-                if (++tries >= kCgTries || full) {
-                    if (lane == 0) atomicOr(a.err, kErrKnnRetry);
-                    failed = true;
-                    break;
-                }
-                R *= fminf(fmaxf(1.25f, 1.1f * cbrtf((float)k / (float)max(cnt, 1))), 8.f);
-            }
-            if (failed) continue;
-            // ------------- selection in the buffer
-            float hi = tau;
-            if (!(hi < INFINITY)) {
-                float m = 0.f;
-                for (int e = lane; e < cnt; e += 32) m = fmaxf(m, bd[e]);
-                hi = cg_wmax(m);
-            }
-            const float vk = wb_select(bd, cnt, k, -1.f, hi, 0, hist, kd, lane, lt);
-            unsigned long long wsum = 0;
-            const float rk = sqrtf(vk);
-            const float inv_h = vk > 0.f ? 2.f / rk : 0.f;
-            for (int e = lane; e < cnt; e += 32) {
-                const float v = bd[e];
-                if (v < vk) {
-                    const float w = m4<float>(sqrtf(v) * inv_h);
-                    wsum += (unsigned long long)(w * 4294967296.0f + 0.5f);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kAll, wsum, o);
-            if (n_out > 0) {
-                // the n_out-th distance, then the entries up to it, ranked by
-                // (d^2, original index)
-                const float vo = n_out == k ? vk : wb_select(bd, cnt, n_out, -1.f, vk, 0, hist, kd, lane, lt);
-                int no = 0;
-                for (int e0 = 0; e0 < cnt; e0 += 32) {
-                    const int e = e0 + lane;
-                    float v = 0.f;
-                    uint32_t sv = 0;
-                    bool in = false;
-                    if (e < cnt) {
-                        v = bd[e];
-                        sv = bs[e];
-                        in = v <= vo;
-                    }
-                    const uint32_t bal = __ballot_sync(kAll, in);
-                    const int pos = no + __popc(bal & lt);
-                    if (in && pos < kOC) {
-                        od[pos] = v;
-                        os[pos] = sv;
-                    }
-                    no += __popc(bal);
-                }
-                __syncwarp();
-                if (no <= kOC) {
-                    if (lane < no) {
-                        const float v = od[lane];
-                        const uint32_t se = os[lane];
-                        uint32_t oe = 0xffffffffu;
-                        int rank = 0;
-                        for (int f = 0; f < no; ++f) {
-                            const float u = od[f];
-                            rank += u < v;
-                            if (u == v && f != lane) {
-                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
-                                rank += __float_as_uint(a.spos[os[f]].w) < oe;
-                            }
-                        }
-                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
-                    }
-                } else {
-                    // more than kOC entries up to the n_out-th: rank in the buffer
-                    for (int e = lane; e < cnt; e += 32) {
-                        const float v = bd[e];
-                        if (!(v <= vo)) continue;
-                        const uint32_t se = bs[e];
-                        uint32_t oe = 0xffffffffu;
-                        int rank = 0;
-                        for (int f = 0; f < cnt; ++f) {
-                            const float u = bd[f];
-                            if (u < v) {
-                                ++rank;
-                                continue;
-                            }
-                            if (u == v && f != e) {
-                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
-                                rank += __float_as_uint(a.spos[bs[f]].w) < oe;
-                            }
-                        }
-                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
-                    }
-                }
-            }
-            if (lane == 0) {
-                float dens;
-                if (vk > 0.f) {
-                    const float h = rk * 0.5f;
-                    dens = (float)(norm * ((float)wsum * 2.3283064365386963e-10f) / (h * h * h));
-                } else {
-                    dens = INFINITY;
-                }
-                a.dens_s[sq] = dens;
-                if (a.rk_s) a.rk_s[sq] = rk;
-            }
-            __syncwarp();
-        }
-    }
-    if (lane == 0) {
-        atomicAdd(&a.counters[kCntCand], cand_acc);
-        atomicAdd(&a.counters[kCntSearch], (unsigned long long)search_acc);
-        atomicAdd(&a.counters[kCntRetry], (unsigned long long)retry_acc);
-        atomicAdd(&a.counters[kCntWarps], (unsigned long long)warp_acc);
-    }
-}
-
-template <bool SEG> int knn_wb_run(hop_ctx *c, const KnnArgs &ka, int cpr)
-{
-    CgDev d;
-    d.spos = (const float4 *)ka.spos;
-    d.keys = ka.keys;
-    d.cellT = ka.cellT;
-    d.level_dense = ka.level_dense;
-    d.n = ka.n;
-    d.n_chunks = SEG ? ka.n_chunks : (ka.n + kWqChunk - 1) / kWqChunk;
-    d.box = (float)ka.box;
-    d.inv_box = (float)(1.0 / ka.box);
-    d.half_box = (float)(0.5 * ka.box);
-    d.norm = (float)(ka.box * ka.box * ka.box / ((double)(ka.n_norm > 0 ? ka.n_norm : ka.n) * 3.14159265358979323846));
-    d.k = ka.k;
-    d.n_out = ka.n_out;
-    d.ld_out = ka.ld_out;
-    d.capq = kWbCap;
-    d.chunk_r = ka.chunk_r;
-    d.plain_r = ka.plain_r;
-    d.cpr = cpr;
-    d.seg = ka.seg;
-    d.B = ka.B;
-    d.nbr_s = ka.nbr_s;
-    d.dens_s = ka.dens_s;
-    d.rk_s = ka.rk_s;
-    d.counters = c->d_counters;
-    d.chunk_counter = c->d_counters + kCntNum;
-    d.err = c->d_err;
-    if (ka.k > kWbCap - 64) return ctx_fail(c, HOP_EINVAL, "n_dens too large for the one-scan buffer");
-    HOP_CUDA(c, cudaMemsetAsync(d.chunk_counter, 0, sizeof(unsigned long long), c->stream));
-    const int warps = kCgWarps;
-    const size_t smem = WbSmem::total * warps;
-    auto kern = knn_wb_kernel<SEG>;
-    HOP_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    HOP_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
-    if (per_sm < 1) return ctx_fail(c, HOP_EINVAL, "kNN buffer does not fit in shared memory");
-    int64_t blocks = (int64_t)per_sm * c->num_sms;
-    const int64_t need = (d.n_chunks + warps - 1) / warps;
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, warps * 32, smem, c->stream>>>(d);
-    HOP_LAUNCH(c);
-    return HOP_OK;
-}
-
 template <bool SEG> int knn_wq_run(hop_ctx *c, const KnnArgs &ka, int cpr)
 {
     CgDev d;
@@ -1885,8 +1451,7 @@ int knn_cg_launch(hop_ctx *c, const KnnArgs &a, int qpw, int cpr)
     switch (qpw) {
     case 16: return a.seg ? knn_cg_run<2, true>(c, a, cpr) : knn_cg_run<2, false>(c, a, cpr);
     case 8: return a.seg ? knn_cg_run<4, true>(c, a, cpr) : knn_cg_run<4, false>(c, a, cpr);
-    case 4: return a.seg ? knn_wb_run<true>(c, a, cpr) : knn_wb_run<false>(c, a, cpr);
-    case 2: return a.seg ? knn_wq_run<true>(c, a, cpr) : knn_wq_run<false>(c, a, cpr);
+    case 4: return a.seg ? knn_wq_run<true>(c, a, cpr) : knn_wq_run<false>(c, a, cpr);
     default: return ctx_fail(c, HOP_EINVAL, "count-then-gather kNN takes 4, 8 or 16 queries per warp");
     }
 }

@@ -51,7 +51,7 @@ def test_512cubed_bench_path_whole_downstream_bit_exact(hop):
     n = len(pos)
     d = torch.from_numpy(pos).cuda()
     p = _learned()
-    cands = [(4, 1, 0), (8, 1, 0), (16, 1, 0), (32, 1, 0)]
+    cands = [(4, 2, 0), (4, 1, 0), (8, 1, 0), (16, 1, 0), (32, 1, 0)]
     best, _ = hop.hop_autotune(d, [0, n], [1.0], p, cands, reps=1)
     assert 0 <= best < len(cands)
     r = hop.hop_run_batch(d, [0, n], [1.0], p, ld_nbr=16)
