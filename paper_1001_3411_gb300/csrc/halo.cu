@@ -11,9 +11,10 @@
 // radius is the largest minimum-image distance from that centre to a member.
 //
 // Four grid-stride passes over the particles, each HBM-bound: peak keys and
-// counts, offset sums, (per group) the centre, then the radii.  Lanes of a
-// warp that hold the same group combine their values with shuffles first,
-// so one atomic per group and warp reaches memory.
+// counts, offset sums, (per group) the centre, then the radii.  A warp
+// reduces each run of consecutive lanes holding the same group with a
+// segmented shuffle scan (five steps), so one atomic per run reaches
+// memory; members of a halo are mostly consecutive in the input.
 #include "hop_internal.cuh"
 
 #include <algorithm>
@@ -36,6 +37,7 @@ __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *
                                  int64_t G, unsigned long long *__restrict__ pkey,
                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ err)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -44,15 +46,15 @@ __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *
             atomicOr(err, kErrBadIndex);
             g = -1;
         }
-        const uint32_t active = __ballot_sync(0xffffffffu, g >= 0);
-        if (g < 0) continue;
-        const uint32_t peers = __match_any_sync(active, g);
+        if (!__any_sync(0xffffffffu, g >= 0)) continue;
+        const uint32_t heads = run_heads((int64_t)g, lane);
         const unsigned long long key =
-            ((unsigned long long)__float_as_uint(dens[i]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
-        const unsigned long long best = peer_max(peers, key);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+            g >= 0 ? ((unsigned long long)__float_as_uint(dens[i]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i)
+                   : 0ull;
+        const unsigned long long best = run_max(heads, lane, key);
+        if (g >= 0 && ((heads >> lane) & 1u)) {
             atomicMax(&pkey[g], best);
-            atomicAdd(&count[g], (unsigned long long)__popc(peers));
+            atomicAdd(&count[g], (unsigned long long)run_len(heads, lane));
         }
     }
 }
@@ -62,21 +64,25 @@ __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__rest
                                 double box, const unsigned long long *__restrict__ pkey,
                                 unsigned long long *__restrict__ sum)
 {
+    const int lane = threadIdx.x & 31;
     const double scale = 4294967296.0 / box;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
         int32_t g = i < n ? group[i] : -1;
         if (g >= G) g = -1;
-        const uint32_t active = __ballot_sync(0xffffffffu, g >= 0);
-        if (g < 0) continue;
-        const uint32_t peers = __match_any_sync(active, g);
-        const int64_t p = (int64_t)(0xFFFFFFFFu - (uint32_t)pkey[g]);
-        long long o[3];
+        if (!__any_sync(0xffffffffu, g >= 0)) continue;
+        const uint32_t heads = run_heads((int64_t)g, lane);
+        long long o[3] = {0, 0, 0};
+        if (g >= 0) {
+            const int64_t p = (int64_t)(0xFFFFFFFFu - (uint32_t)pkey[g]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            o[d] = peer_sum_ll(peers, __double2ll_rn(min_image_d(coord(pos, i, d) - coord(pos, p, d), box) * scale));
-        if ((threadIdx.x & 31) == __ffs(peers) - 1)
+            for (int d = 0; d < 3; ++d)
+                o[d] = __double2ll_rn(min_image_d(coord(pos, i, d) - coord(pos, p, d), box) * scale);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) o[d] = run_sum<long long>(heads, lane, o[d]);
+        if (g >= 0 && ((heads >> lane) & 1u))
             for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g + d], (unsigned long long)o[d]);
     }
 }
@@ -109,23 +115,27 @@ template <typename T>
 __global__ void halo_radius_kernel(const T *__restrict__ pos, const int32_t *__restrict__ group, int64_t n, int64_t G,
                                    double box, const double *__restrict__ com, unsigned long long *__restrict__ rbits)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
         int32_t g = i < n ? group[i] : -1;
         if (g >= G) g = -1;
-        const uint32_t active = __ballot_sync(0xffffffffu, g >= 0);
-        if (g < 0) continue;
-        const uint32_t peers = __match_any_sync(active, g);
-        double r2 = 0.0;
+        if (!__any_sync(0xffffffffu, g >= 0)) continue;
+        const uint32_t heads = run_heads((int64_t)g, lane);
+        unsigned long long b = 0;
+        if (g >= 0) {
+            double r2 = 0.0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const double dx = min_image_d(coord(pos, i, d) - com[3 * (int64_t)g + d], box);
-            r2 += dx * dx;
+            for (int d = 0; d < 3; ++d) {
+                const double dx = min_image_d(coord(pos, i, d) - com[3 * (int64_t)g + d], box);
+                r2 += dx * dx;
+            }
+            // non-negative doubles order like their bit patterns
+            b = (unsigned long long)__double_as_longlong(sqrt(r2));
         }
-        // non-negative doubles order like their bit patterns
-        const unsigned long long b = peer_max(peers, (unsigned long long)__double_as_longlong(sqrt(r2)));
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&rbits[g], b);
+        b = run_max(heads, lane, b);
+        if (g >= 0 && ((heads >> lane) & 1u)) atomicMax(&rbits[g], b);
     }
 }
 

@@ -269,6 +269,44 @@ __device__ __forceinline__ unsigned long long peer_max(uint32_t peers, unsigned 
     return b;
 }
 
+// Runs of consecutive lanes with the same group key g (each run reduced by
+// one atomic): heads has a bit for every lane that starts a run.
+__device__ __forceinline__ uint32_t run_heads(int64_t g, int lane)
+{
+    const int64_t prev = __shfl_up_sync(0xffffffffu, g, 1);
+    return __ballot_sync(0xffffffffu, lane == 0 || prev != g);
+}
+
+// After it, the head of each run holds the sum (or maximum) of the run's
+// values: a suffix scan over the run in five shuffle steps, adding lane + d
+// while no run starts in (lane, lane + d].
+template <typename V> __device__ __forceinline__ V run_sum(uint32_t heads, int lane, V v)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const V o = __shfl_down_sync(0xffffffffu, v, d);
+        const uint32_t between = lane + d < 32 ? ((2u << (lane + d)) - (2u << lane)) : 0u;
+        if (lane + d < 32 && (heads & between) == 0) v += o;
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long run_max(uint32_t heads, int lane, unsigned long long v)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, v, d);
+        const uint32_t between = lane + d < 32 ? ((2u << (lane + d)) - (2u << lane)) : 0u;
+        if (lane + d < 32 && (heads & between) == 0 && o > v) v = o;
+    }
+    return v;
+}
+// Lanes in the run that starts at this head lane.
+__device__ __forceinline__ int run_len(uint32_t heads, int lane)
+{
+    const uint32_t after = lane < 31 ? heads >> (lane + 1) : 0u;
+    return after ? __ffs(after) : 32 - lane;
+}
+
 // A size known only on the device (an edge or chain count): kernels read
 // *dev when it is set, so a captured graph needs no host round trip; `max`
 // bounds it and sizes the grid.

@@ -1059,6 +1059,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
             bool certified = false, failed = false, full = false;
             float qx = rqx, qy = rqy, qz = rqz;
             bool fx = false, fy = false, fz = false;   // frame shift per axis
+            bool shifted = false;                      // any of them (warp-uniform)
             int nc = 0, l = 1;
             uint32_t total = 0;
             int top = 0, shift = kShift0, top0 = 0;
@@ -1079,6 +1080,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
                     qx = (fx && rqx >= half) ? rqx - box : rqx;
                     qy = (fy && rqy >= half) ? rqy - box : rqy;
                     qz = (fz && rqz >= half) ? rqz - box : rqz;
+                    shifted = fx || fy || fz;
                     if (full) {
                         if (lane == 0) {
                             cra[0] = (uint32_t)seg_base;
@@ -1118,10 +1120,14 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
                             dx = wrapdiff(v.x, rqx, box, half);
                             dy = wrapdiff(v.y, rqy, box, half);
                             dz = wrapdiff(v.z, rqz, box, half);
-                        } else {
+                        } else if (shifted) {
                             dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
                             dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
                             dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
+                        } else {
+                            dx = v.x - qx;
+                            dy = v.y - qy;
+                            dz = v.z - qz;
                         }
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (d2 <= tauA) {
@@ -1223,10 +1229,14 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
                             dx = wrapdiff(v.x, rqx, box, half);
                             dy = wrapdiff(v.y, rqy, box, half);
                             dz = wrapdiff(v.z, rqz, box, half);
-                        } else {
+                        } else if (shifted) {
                             dx = (fx && v.x >= half ? v.x - box : v.x) - qx;
                             dy = (fy && v.y >= half ? v.y - box : v.y) - qy;
                             dz = (fz && v.z >= half ? v.z - box : v.z) - qz;
+                        } else {
+                            dx = v.x - qx;
+                            dy = v.y - qy;
+                            dz = v.z - qz;
                         }
                         d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     }

@@ -23,6 +23,7 @@
 #include "hop_internal.cuh"
 
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 namespace {
@@ -117,6 +118,7 @@ __global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const
                                     unsigned long long *__restrict__ cnt, double *__restrict__ sum,
                                     unsigned long long *__restrict__ pkey)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -127,13 +129,13 @@ __global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const
             const uint32_t c = pc[i];
             if (c != kNone && key_dens(k) >= ds) r = parent[c];
         }
-        const uint32_t active = __ballot_sync(0xffffffffu, r != kNone);
-        if (r == kNone) continue;
-        const uint32_t peers = __match_any_sync(active, r);
-        const double s = sum ? peer_sum_f64(peers, (double)key_dens(k)) : 0.0;
-        const unsigned long long best = peer_max(peers, k);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) {
-            atomicAdd(&cnt[r], (unsigned long long)__popc(peers));
+        if (!__any_sync(0xffffffffu, r != kNone)) continue;
+        // runs of consecutive lanes in one component: one atomic per run
+        const uint32_t heads = run_heads((int64_t)r, lane);
+        const double s = sum ? run_sum<double>(heads, lane, r != kNone ? (double)key_dens(k) : 0.0) : 0.0;
+        const unsigned long long best = run_max(heads, lane, r != kNone ? k : 0ull);
+        if (r != kNone && ((heads >> lane) & 1u)) {
+            atomicAdd(&cnt[r], (unsigned long long)run_len(heads, lane));
             if (sum) atomicAdd(&sum[r], s);
             atomicMax(&pkey[r], best);
         }
@@ -180,8 +182,9 @@ __global__ void sub_list_kernel(int64_t C, const uint32_t *__restrict__ flag, co
     }
 }
 
-__global__ void sub_rank_kernel(int64_t G, const uint32_t *__restrict__ gv, uint32_t *__restrict__ rank)
+__global__ void sub_rank_kernel(DevCount Gc, const uint32_t *__restrict__ gv, uint32_t *__restrict__ rank)
 {
+    const int64_t G = Gc.get();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x)
         rank[gv[g]] = (uint32_t)g;
@@ -217,12 +220,13 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
     HOP_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
     // S2
     uint32_t *hp = (uint32_t *)c->h_pinned;
-    uint32_t *misc = (uint32_t *)ctx_buf(c, S_MISC, 256);
+    // misc: total, then kMaxRounds round flags, then one group count per level
+    uint32_t *misc = (uint32_t *)ctx_buf(c, S_MISC, (size_t)(2 + kMaxRounds + L) * sizeof(uint32_t));
     uint32_t *cid = (uint32_t *)ctx_buf(c, S_SUB, (size_t)(2 * n + 64) * sizeof(uint32_t));
     if (!misc || !cid) return HOP_ENOMEM;
     uint32_t *pc = cid + ((n + 1 + 63) & ~int64_t(63));
-    uint32_t *d_total = misc, *d_changed = misc + 1;
-    HOP_CUDA(c, cudaMemsetAsync(misc, 0, 16, c->stream));
+    uint32_t *d_total = misc, *d_flags = misc + 2, *d_levG = misc + 2 + kMaxRounds;
+    HOP_CUDA(c, cudaMemsetAsync(misc, 0, (size_t)(2 + kMaxRounds + L) * sizeof(uint32_t), c->stream));
     sub_root_flag_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(chain, dkey, n, d_o, cid, c->d_err);
     HOP_LAUNCH(c);
     rc = scan_exclusive_u32(c, cid, cid, n, d_total);
@@ -258,29 +262,37 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
     if (rc) return rc;
     c->stats.n_chains = C;
     c->stats.n_edges = m;
+    // Each level runs without host round trips except the convergence test
+    // of its component rounds, read once per batch of kRoundBatch rounds
+    // (rounds after convergence change nothing); group counts stay on the
+    // device until every level is enqueued.
+    constexpr int kRoundBatch = 4;
     for (int l = 0; l < L; ++l) {
         const float ds = levels[l];
         int32_t *out = sub + (int64_t)l * n;
         if (C == 0) {
             HOP_CUDA(c, cudaMemsetAsync(out, 0xFF, n * sizeof(int32_t), c->stream));
-            n_sub[l] = 0;
             continue;
         }
         // S3
         sub_iota_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
         HOP_LAUNCH(c);
         int rounds = 0;
-        for (; m > 0 && rounds < kMaxRounds; ++rounds) {
-            HOP_CUDA(c, cudaMemsetAsync(d_changed, 0, 4, c->stream));
-            sub_hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ea, eb, es, m, 2.0 * (double)ds, parent, d_changed);
-            HOP_LAUNCH(c);
-            sub_compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
-            HOP_LAUNCH(c);
-            HOP_CUDA(c, cudaMemcpyAsync(hp + 1, d_changed, 4, cudaMemcpyDeviceToHost, c->stream));
+        bool converged = m == 0;
+        while (!converged) {
+            if (rounds + kRoundBatch > kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "subhalo components did not converge");
+            HOP_CUDA(c, cudaMemsetAsync(d_flags + rounds, 0, kRoundBatch * sizeof(uint32_t), c->stream));
+            for (int b = 0; b < kRoundBatch; ++b, ++rounds) {
+                sub_hook_kernel<<<grid_for(c, m), 256, 0, c->stream>>>(ea, eb, es, m, 2.0 * (double)ds, parent,
+                                                                       d_flags + rounds);
+                HOP_LAUNCH(c);
+                sub_compress_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(parent, C);
+                HOP_LAUNCH(c);
+            }
+            HOP_CUDA(c, cudaMemcpyAsync(hp + 1, d_flags + rounds - 1, 4, cudaMemcpyDeviceToHost, c->stream));
             HOP_CUDA(c, cudaStreamSynchronize(c->stream));
-            if (!hp[1]) break;
+            converged = hp[1] == 0;
         }
-        if (rounds >= kMaxRounds) return ctx_fail(c, HOP_ETIMEOUT, "subhalo components did not converge");
         // S4
         double *lsum = (f > 0.0 || n >= (int64_t(1) << 29)) ? sum : nullptr;
         HOP_CUDA(c, cudaMemsetAsync(cnt, 0, C * 8, c->stream));
@@ -288,29 +300,29 @@ int subhalos(hop_ctx *c, const uint32_t *chain, const uint64_t *dkey, const uint
         HOP_CUDA(c, cudaMemsetAsync(pkey, 0, C * 8, c->stream));
         sub_member_stats_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, cnt, lsum, pkey);
         HOP_LAUNCH(c);
-        // S5
+        // S5: accepted components, ranked by peak; their count stays on the device
         sub_accept_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, parent, cnt, lsum, (double)ds, (long long)n_min,
                                                                  f, flag);
         HOP_LAUNCH(c);
-        rc = scan_exclusive_u32(c, flag, gpos, C, d_total);
+        rc = scan_exclusive_u32(c, flag, gpos, C, d_levG + l);
         if (rc) return rc;
-        HOP_CUDA(c, cudaMemcpyAsync(hp, d_total, 4, cudaMemcpyDeviceToHost, c->stream));
-        HOP_CUDA(c, cudaStreamSynchronize(c->stream));
-        const int64_t G = hp[0];
-        if (G > 0) {
-            sub_list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, pkey, gk0, gv0);
-            HOP_LAUNCH(c);
-            uint64_t *gk = gk0, *gkb = gkb0;
-            uint32_t *gv = gv0, *gvb = gvb0;
-            rc = radix_sort_u64(c, gk, gkb, gv, gvb, G, 0, 64, tmp);
-            if (rc) return rc;
-            sub_rank_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, gv, rank);
-            HOP_LAUNCH(c);
-        }
+        const DevCount G{C, d_levG + l};
+        sub_list_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(C, flag, gpos, pkey, gk0, gv0);
+        HOP_LAUNCH(c);
+        uint64_t *gk = gk0, *gkb = gkb0;
+        uint32_t *gv = gv0, *gvb = gvb0;
+        rc = radix_sort_u64_dev(c, gk, gkb, gv, gvb, G, 0, 64, tmp);
+        if (rc) return rc;
+        sub_rank_kernel<<<grid_for(c, C), 256, 0, c->stream>>>(G, gv, rank);
+        HOP_LAUNCH(c);
         sub_label_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dkey, pc, n, ds, parent, flag, rank, out);
         HOP_LAUNCH(c);
-        n_sub[l] = G;
     }
+    std::vector<uint32_t> levG(L);
+    HOP_CUDA(c, cudaMemcpyAsync(levG.data(), d_levG, (size_t)L * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+    HOP_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int l = 0; l < L; ++l) n_sub[l] = C == 0 ? 0 : (int64_t)levG[l];
     return HOP_OK;
 }
 

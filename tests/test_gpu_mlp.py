@@ -70,15 +70,16 @@ def test_training_on_the_gpu_fits_the_radii(hop, samples):
 
 def test_trained_network_gains_over_plain_and_closed_form(hop):
     """Same output, fewer candidates: the stored network (trained on the
-    256^3 box) against the plain base-grid radius and the closed-form
-    count-based radius, on a fresh 2M-particle box."""
+    256^3 box) against the plain mean-density radius and the closed-form
+    count-based radius, on a fresh 2M-particle box, in the benchmark's
+    kernel configuration (one warp per query, 4 queries per chunk)."""
     pos = torch.from_numpy(synth.nfw_box(2_000_000, 93)[0]).cuda()
     n = pos.shape[0]
     res = {}
     for name, mode in (("plain", 0), ("count", 1), ("learned", 2)):
-        hop.set_tuning(8, 1)
+        hop.apply_tuning(4, 2, 0)
         if mode == 2:
-            w, m = radius_model.load()[8]
+            w, m = radius_model.load()[4]
             hop.hop_mlp_load(w, m)
         r = hop.hop_run(pos, hopgpu.default_params(radius_mode=mode))
         st = hop.stats()
