@@ -377,6 +377,49 @@ __device__ __forceinline__ void rows_find(const int *hist, int q, int p, int ran
     upto = gsum<P>(fupto);
 }
 
+// The rank-th smallest of a query's list entries above lo when more than
+// kKC of them share its bin: a radix descent on the bit pattern of d^2 (4
+// bits per level, a 16-bin histogram in h16 per level).  Kept out of line:
+// crowded bins are rare, and the common path stays small.
+template <int P>
+__device__ __noinline__ float list_kth_deep(bool deep, const float *Ld, int cnt, int cmax, float lo, int below,
+                                            int rank, int *h16, int p)
+{
+    uint32_t pfx = 0;
+    int bel = below;
+    for (int sh = 28; sh >= 0; sh -= 4) {
+        __syncwarp();
+        if (deep)
+            for (int i = p; i < 16; i += P) h16[i] = 0;
+        __syncwarp();
+        for (int e0 = 0; e0 < cmax; e0 += P) {
+            const int e = e0 + p;
+            if (deep && e < cnt) {
+                const float v = Ld[e];
+                const uint32_t u = __float_as_uint(v);
+                if (v > lo && (sh == 28 || (u >> (sh + 4)) == pfx)) atomicAdd(&h16[(u >> sh) & 15], 1);
+            }
+        }
+        __syncwarp();
+        if (deep) {
+            int cum = bel, dsel = 15, dbel = bel;
+            for (int i = 0; i < 16; ++i) {
+                const int hh = h16[i];
+                if (cum + hh >= rank) {
+                    dsel = i;
+                    dbel = cum;
+                    break;
+                }
+                cum += hh;
+            }
+            pfx = (pfx << 4) | (uint32_t)dsel;
+            bel = dbel;
+        }
+    }
+    __syncwarp();
+    return __uint_as_float(pfx);
+}
+
 // Exact rank-th smallest d^2 of a query's list: its entries in (lo, hi] are
 // the bin holding it, with `below` smaller entries outside the bin.  Up to
 // kKC entries are gathered and ranked; a larger bin goes through a radix
@@ -421,41 +464,8 @@ __device__ float list_kth(bool member, const float *Ld, int cnt, int cmax, float
         if (mine && l0 < rank && rank <= le) vk = v;
     }
     if (__any_sync(kAll, member && !small)) {
-        const bool deep = member && !small;
-        int *h16 = (int *)kd;   // the small list overflowed: its room is free
-        uint32_t pfx = 0;
-        int bel = below;
-        for (int sh = 28; sh >= 0; sh -= 4) {
-            __syncwarp();
-            if (deep)
-                for (int i = p; i < 16; i += P) h16[i] = 0;
-            __syncwarp();
-            for (int e0 = 0; e0 < cmax; e0 += P) {
-                const int e = e0 + p;
-                if (deep && e < cnt) {
-                    const float v = Ld[e];
-                    const uint32_t u = __float_as_uint(v);
-                    if (v > lo && (sh == 28 || (u >> (sh + 4)) == pfx)) atomicAdd(&h16[(u >> sh) & 15], 1);
-                }
-            }
-            __syncwarp();
-            if (deep) {
-                int cum = bel, dsel = 15, dbel = bel;
-                for (int i = 0; i < 16; ++i) {
-                    const int hh = h16[i];
-                    if (cum + hh >= rank) {
-                        dsel = i;
-                        dbel = cum;
-                        break;
-                    }
-                    cum += hh;
-                }
-                pfx = (pfx << 4) | (uint32_t)dsel;
-                bel = dbel;
-            }
-        }
-        __syncwarp();
-        if (deep) vk = __uint_as_float(pfx);
+        const float vd = list_kth_deep<P>(member && !small, Ld, cnt, cmax, lo, below, rank, (int *)kd, p);
+        if (member && !small) vk = vd;
     }
     return gmaxf<P>(vk);
 }
@@ -952,13 +962,14 @@ __device__ __forceinline__ uint32_t wq_prefix(const uint32_t *cln, uint32_t *cpr
 // Visits the particles of cells [0, nc) (ranges cra/cln, prefix cpre), 32
 // consecutive ones per step, lane t taking particle g0 + t: fn(v, s, valid).
 // The cell of each lane's particle comes from the cell starts inside the
-// step's window (one bit each), so no lane searches the prefix.  Four steps
-// issue their loads before the first is used.
+// step's window (one bit each), so no lane searches the prefix.  (Issuing
+// several steps' loads ahead measured slower: the larger loop body costs
+// more in instruction fetch and registers than the overlap gains.)
 template <typename F>
 __device__ __forceinline__ void wq_visit(const float4 *__restrict__ spos, const uint32_t *cra, const uint32_t *cpre,
                                          int nc, uint32_t total, int lane, F &&fn)
 {
-    constexpr int U = 4;
+    constexpr int U = 1;
     int cbase = -1;   // the cell holding particle g0 - 1
     const uint32_t upto_lane = lane == 31 ? kAll : ((2u << lane) - 1u);
     for (uint32_t g0 = 0; g0 < total; g0 += 32 * U) {
@@ -983,6 +994,34 @@ __device__ __forceinline__ void wq_visit(const float4 *__restrict__ spos, const 
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) fn(v[u], s[u], s[u] != 0xffffffffu);
+    }
+}
+
+// The n_out nearest of a warp's list when more than kOC entries lie up to
+// the n_out-th bin (long Nhop lists, ties): each entry up to edge_o is
+// ranked by (d^2, original index) against the whole list.  Out of line: the
+// common path gathers at most kOC entries instead.
+__device__ __noinline__ void wq_rank_in_list(const float *Ld, const uint32_t *Ls, int cnt, float edge_o, int n_out,
+                                             const float4 *__restrict__ spos, uint32_t *row, int lane)
+{
+    for (int e = lane; e < cnt; e += 32) {
+        const float v = Ld[e];
+        if (!(v <= edge_o)) continue;
+        const uint32_t se = Ls[e];
+        uint32_t oe = 0xffffffffu;
+        int rank = 0;
+        for (int f = 0; f < cnt; ++f) {
+            const float u = Ld[f];
+            if (u < v) {
+                ++rank;
+                continue;
+            }
+            if (u == v && f != e) {
+                if (oe == 0xffffffffu) oe = __float_as_uint(spos[se].w);
+                rank += __float_as_uint(spos[Ls[f]].w) < oe;
+            }
+        }
+        if (rank < n_out) row[rank] = se;
     }
 }
 
@@ -1309,26 +1348,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
                         if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
                     }
                 } else {
-                    // many entries up to the n_out-th bin: rank in the list itself
-                    for (int e = lane; e < cnt; e += 32) {
-                        const float v = Ld[e];
-                        if (!(v <= edge_o)) continue;
-                        const uint32_t se = Ls[e];
-                        uint32_t oe = 0xffffffffu;
-                        int rank = 0;
-                        for (int f = 0; f < cnt; ++f) {
-                            const float u = Ld[f];
-                            if (u < v) {
-                                ++rank;
-                                continue;
-                            }
-                            if (u == v && f != e) {
-                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
-                                rank += __float_as_uint(a.spos[Ls[f]].w) < oe;
-                            }
-                        }
-                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
-                    }
+                    wq_rank_in_list(Ld, Ls, cnt, edge_o, n_out, a.spos, a.nbr_s + (size_t)sq * a.ld_out, lane);
                 }
             }
             if (lane == 0) {
