@@ -487,8 +487,8 @@ def run_gb300(args):
                "roofline_level": {"bound": "hbm", "achieved": lbytes / (ms_lv * 1e-3) / 1e9, "peak": hbm,
                                   "unit": "GB/s", "frac": lbytes / (ms_lv * 1e-3) / 1e9 / hbm, "traffic": None,
                                   "basis": "28 B per particle per level (density key and chain id read twice, "
-                                           "label written); the level time includes its host-driven "
-                                           "component rounds"}}
+                                           "label written); the level time includes its component "
+                                           "rounds, whose convergence the host reads once per four rounds"}}
         del r
         torch.cuda.empty_cache()
 

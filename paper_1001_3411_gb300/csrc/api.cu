@@ -72,6 +72,7 @@ int ctx_check_device_error(hop_ctx *c)
     if (e & kErrMergeLoop) return ctx_fail(c, HOP_ETIMEOUT, "merge rounds did not converge");
     if (e & kErrTableFull) return ctx_fail(c, HOP_ENOMEM, "boundary table full");
     if (e & kErrChainCap) return ctx_fail(c, HOP_ENOMEM, "more chains than the merge arrays hold");
+    if (e & kErrSortWait) return ctx_fail(c, HOP_ETIMEOUT, "a radix sort pass waited too long for an earlier tile");
     return ctx_fail(c, HOP_ECUDA, "device error word " + std::to_string(e));
 }
 

@@ -84,16 +84,42 @@ __global__ void gather_kernel(const T *__restrict__ pos, const uint32_t *__restr
     }
 }
 
+// Every lane holds a run t[lo, hi) to fill with v (empty when !act).  Runs
+// of up to 32 entries are written by their lane; longer ones (the empty
+// cells of voids) by the whole warp, 32 consecutive entries per store.
+__device__ __forceinline__ void fill_runs(uint32_t *t, int64_t lo, int64_t hi, uint32_t v, bool act)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const bool big = act && hi - lo > 32;
+    if (act && !big)
+        for (int64_t c = lo; c < hi; ++c) t[c] = v;
+    unsigned m = __ballot_sync(0xffffffffu, big);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        uint32_t *tt = (uint32_t *)__shfl_sync(0xffffffffu, (unsigned long long)t, src);
+        const int64_t a = __shfl_sync(0xffffffffu, lo, src), b = __shfl_sync(0xffffffffu, hi, src);
+        const uint32_t vv = __shfl_sync(0xffffffffu, v, src);
+        for (int64_t c = a + lane; c < b; c += 32) tt[c] = vv;
+    }
+}
+
 // cellT[c] = first sorted index whose dense-level cell is >= c, for
-// c = 0 .. ncell (cellT[ncell] = n).
+// c = 0 .. ncell (cellT[ncell] = n); position s writes the cells after its
+// predecessor's up to its own.
 __global__ void cell_table_kernel(const uint64_t *__restrict__ keys, int64_t n, int shift,
                                   int64_t ncell, uint32_t *__restrict__ cellT)
 {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t cs = s < n ? (int64_t)(keys[s] >> shift) : ncell;
-        const int64_t cp = s > 0 ? (int64_t)(keys[s - 1] >> shift) : -1;
-        for (int64_t c = cp + 1; c <= cs; ++c) cellT[c] = (uint32_t)s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); s0 <= n; s0 += stride) {
+        const int64_t s = s0 + (threadIdx.x & 31u);
+        const bool act = s <= n;
+        int64_t cs = 0, cp = 0;
+        if (act) {
+            cs = s < n ? (int64_t)(keys[s] >> shift) : ncell;
+            cp = s > 0 ? (int64_t)(keys[s - 1] >> shift) : -1;
+        }
+        fill_runs(cellT, cp + 1, cs + 1, (uint32_t)s, act);
     }
 }
 
@@ -104,18 +130,25 @@ __global__ void cell_table_seg_kernel(const uint64_t *__restrict__ keys, int64_t
                                       const SegDesc *__restrict__ seg, uint32_t *__restrict__ cellT)
 {
     const uint64_t m48 = (uint64_t(1) << 48) - 1;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = keys[s];
-        const SegDesc &d = seg[key >> 48];
-        const int shift = 3 * (kMaxLevel - d.level_dense);
-        const int64_t ncell = int64_t(1) << (3 * d.level_dense);
-        uint32_t *t = cellT + d.cell0;
-        const int64_t cs = (int64_t)((key & m48) >> shift);
-        const int64_t cp = s > d.base ? (int64_t)((keys[s - 1] & m48) >> shift) : -1;
-        for (int64_t c = cp + 1; c <= cs; ++c) t[c] = (uint32_t)s;
-        if (s == d.base + d.n - 1)
-            for (int64_t c = cs + 1; c <= ncell; ++c) t[c] = (uint32_t)(s + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); s0 < n; s0 += stride) {
+        const int64_t s = s0 + (threadIdx.x & 31u);
+        const bool act = s < n;
+        uint32_t *t = cellT;
+        int64_t cs = 0, cp = 0, ncell = 0;
+        bool last = false;
+        if (act) {
+            const uint64_t key = keys[s];
+            const SegDesc &d = seg[key >> 48];
+            const int shift = 3 * (kMaxLevel - d.level_dense);
+            ncell = int64_t(1) << (3 * d.level_dense);
+            t = cellT + d.cell0;
+            cs = (int64_t)((key & m48) >> shift);
+            cp = s > d.base ? (int64_t)((keys[s - 1] & m48) >> shift) : -1;
+            last = s == d.base + d.n - 1;
+        }
+        fill_runs(t, cp + 1, cs + 1, (uint32_t)s, act);
+        fill_runs(t, cs + 1, ncell + 1, (uint32_t)(s + 1), last);
     }
 }
 

@@ -29,6 +29,7 @@ enum : uint32_t {
     kErrMergeLoop = 1u << 5,    // merge rounds hit their limit
     kErrBadIndex = 1u << 6,     // an index array holds a value >= n
     kErrChainCap = 1u << 7,     // more chains above delta_outer than a batched pass's merge arrays hold
+    kErrSortWait = 1u << 8,     // a radix pass's look-back wait hit its limit
 };
 
 // Scratch slots owned by a context.  Each slot grows on demand.
