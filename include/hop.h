@@ -290,11 +290,12 @@ int hop_link_static(const float *dens, const uint32_t *nbr, int32_t ld_nbr, int6
  * is its member count.  In the periodic box the centre of mass is taken
  * about the halo's peak particle (its densest member, then the smaller
  * index): the members' minimum-image offsets from the peak are averaged and
- * added to the peak's position, then wrapped into [0, box).  The offsets
- * are summed in fixed point (2^-32 of the box), so centres are reproducible
- * and within 2^-33 of the box of the exact mean.  The
- * maximum radius is the largest minimum-image distance from that centre to
- * a member.  All pointers are device memory, in the caller's order:
+ * added to the peak's position, then wrapped into [0, box).  The maximum
+ * radius is the largest minimum-image distance from that centre to a
+ * member.  Coordinates are taken in fixed point (2^-32 of the box, rounded
+ * once), so centres are reproducible and within 2^-33 of the box of the
+ * exact mean, and radii within 1.5 x 2^-32 of the box of the exact
+ * distance.  All pointers are device memory, in the caller's order:
  *   pos    n x 3 float32 (float64 if pos_is_f64), as given to hop_run;
  *   dens   n float32; group n int32 (-1 = no halo, else < n_groups);
  *   count  n_groups int64, peak n_groups uint32 (particle index),

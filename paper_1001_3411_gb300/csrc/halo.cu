@@ -4,14 +4,22 @@
 // is the member count.  In the periodic box the centre of mass is taken
 // about the halo's peak particle (its densest member, then the smaller
 // index): members' minimum-image offsets from the peak are averaged and
-// added to the peak's position, wrapped into [0, box).  The offsets are
-// summed in fixed point (2^-32 of the box, int64 atomics), so the centres do
-// not depend on the order of the sums and lie within 2^-33 of the box of
-// the exact mean.  The maximum
-// radius is the largest minimum-image distance from that centre to a member.
+// added to the peak's position, wrapped into [0, box).
 //
-// Four grid-stride passes over the particles, each HBM-bound: peak keys and
-// counts, offset sums, (per group) the centre, then the radii.  A warp
+// Arithmetic.  Coordinates are taken in fixed point, X = rn(x 2^32 / box)
+// (int64, within 0.5 + 2^-12 units of the exact value), so the box is
+// 2^32 units and minimum images are integer wraps.  The centre is the
+// peak's X plus the mean of the members' wrapped offsets from it -- the
+// mean of the members' unwrapped X, within 0.5 units of the exact centre
+// whatever the order of the sums.  The maximum radius is the largest
+// member distance from the centre rounded to units, its square summed
+// exactly in uint64: within 1.5 units of the exact distance.  No per-member
+// arithmetic runs in fp64 (GB300's fp64 rate is a small fraction of its
+// fp32 rate); the split scale makes the fp32 product exact enough.
+//
+// Three grid-stride passes over the particles, each HBM-bound: peak keys
+// and counts, offset sums, then the radii; between them, per group, the
+// peak's coordinates and the centre.  A warp
 // reduces each run of consecutive lanes holding the same group with a
 // segmented shuffle scan (five steps), so one atomic per run reaches
 // memory; members of a halo are mostly consecutive in the input.
@@ -21,149 +29,242 @@
 
 namespace {
 
-__device__ __forceinline__ double min_image_d(double dx, double box)
+constexpr long long kUnits = 1ll << 32;   // the box in fixed-point units
+
+// rn(x * scale) for x in [0, box): the scale is split into two floats
+// (hi + lo); x hi is exact as p + e (fmaf), and e + x lo is small, so one
+// more rounding of the fractional part gives the integer.
+__device__ __forceinline__ long long fixed_of(float x, float s_hi, float s_lo)
 {
-    if (dx > 0.5 * box) return dx - box;
-    if (dx < -0.5 * box) return dx + box;
-    return dx;
+    const float p = x * s_hi;
+    const float e = fmaf(x, s_hi, -p);
+    const float t = fmaf(x, s_lo, e);
+    const float pi = rintf(p);
+    return (long long)pi + (long long)rintf((p - pi) + t);
 }
 
-template <typename T> __device__ __forceinline__ double coord(const T *pos, int64_t i, int d)
+__device__ __forceinline__ long long fixed_of(double x, float, float, double s) { return __double2ll_rn(x * s); }
+__device__ __forceinline__ long long fixed_of(float x, float s_hi, float s_lo, double)
 {
-    return (double)pos[3 * i + d];
+    return fixed_of(x, s_hi, s_lo);
 }
+
+__device__ __forceinline__ long long wrap_units(long long d)
+{
+    if (d > kUnits / 2) return d - kUnits;
+    if (d < -kUnits / 2) return d + kUnits;
+    return d;
+}
+
+struct Scale {
+    double s;          // 2^32 / box
+    float hi, lo;      // s split into two floats
+};
+
+// Each pass takes the particles in batches of kHaloU blocks' width per
+// block: a thread loads its kHaloU elements' group ids (and the data they
+// need) before any of them is reduced, so the loads of a batch overlap.
+constexpr int kHaloU = 4;
 
 __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *__restrict__ group, int64_t n,
                                  int64_t G, unsigned long long *__restrict__ pkey,
                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ err)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        int32_t g = i < n ? group[i] : -1;
-        if (g >= G) {
-            atomicOr(err, kErrBadIndex);
-            g = -1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
+        int32_t g[kHaloU];
+        float dv[kHaloU];
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            g[u] = i < n ? group[i] : -1;
+            dv[u] = i < n ? dens[i] : 0.f;
         }
-        if (!__any_sync(0xffffffffu, g >= 0)) continue;
-        const uint32_t heads = run_heads((int64_t)g, lane);
-        const unsigned long long key =
-            g >= 0 ? ((unsigned long long)__float_as_uint(dens[i]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i)
-                   : 0ull;
-        const unsigned long long best = run_max(heads, lane, key);
-        if (g >= 0 && ((heads >> lane) & 1u)) {
-            atomicMax(&pkey[g], best);
-            atomicAdd(&count[g], (unsigned long long)run_len(heads, lane));
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            int32_t gg = g[u];
+            if (gg >= G) {
+                atomicOr(err, kErrBadIndex);
+                gg = -1;
+            }
+            if (!__any_sync(0xffffffffu, gg >= 0)) continue;
+            const uint32_t heads = run_heads((int64_t)gg, lane);
+            const unsigned long long key =
+                gg >= 0 ? ((unsigned long long)__float_as_uint(dv[u]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i)
+                        : 0ull;
+            const unsigned long long best = run_max(heads, lane, key);
+            if (gg >= 0 && ((heads >> lane) & 1u)) {
+                atomicMax(&pkey[gg], best);
+                atomicAdd(&count[gg], (unsigned long long)run_len(heads, lane));
+            }
         }
+    }
+}
+
+// Per group: the peak's fixed-point coordinates (xp, 3 per group).
+template <typename T>
+__global__ void halo_peak_pos_kernel(const T *__restrict__ pos, int64_t G, Scale sc,
+                                     const unsigned long long *__restrict__ pkey,
+                                     const unsigned long long *__restrict__ cnt, long long *__restrict__ xp)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = cnt[g] ? (int64_t)(0xFFFFFFFFu - (uint32_t)pkey[g]) : 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) xp[3 * g + d] = cnt[g] ? fixed_of(pos[3 * p + d], sc.hi, sc.lo, sc.s) : 0;
     }
 }
 
 template <typename T>
 __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__restrict__ group, int64_t n, int64_t G,
-                                double box, const unsigned long long *__restrict__ pkey,
-                                unsigned long long *__restrict__ sum)
+                                Scale sc, const long long *__restrict__ xp, unsigned long long *__restrict__ sum)
 {
     const int lane = threadIdx.x & 31;
-    const double scale = 4294967296.0 / box;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        int32_t g = i < n ? group[i] : -1;
-        if (g >= G) g = -1;
-        if (!__any_sync(0xffffffffu, g >= 0)) continue;
-        const uint32_t heads = run_heads((int64_t)g, lane);
-        long long o[3] = {0, 0, 0};
-        if (g >= 0) {
-            const int64_t p = (int64_t)(0xFFFFFFFFu - (uint32_t)pkey[g]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
+        int32_t g[kHaloU];
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-                o[d] = __double2ll_rn(min_image_d(coord(pos, i, d) - coord(pos, p, d), box) * scale);
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            g[u] = i < n ? group[i] : -1;
+            if (g[u] >= G) g[u] = -1;
+        }
+        T x[kHaloU][3];
+        long long c[kHaloU][3];
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
+                c[u][d] = g[u] >= 0 ? xp[3 * (int64_t)g[u] + d] : 0;
+            }
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) o[d] = run_sum<long long>(heads, lane, o[d]);
-        if (g >= 0 && ((heads >> lane) & 1u))
-            for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g + d], (unsigned long long)o[d]);
+        for (int u = 0; u < kHaloU; ++u) {
+            if (!__any_sync(0xffffffffu, g[u] >= 0)) continue;
+            const uint32_t heads = run_heads((int64_t)g[u], lane);
+            long long o[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                o[d] = g[u] >= 0 ? wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]) : 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) o[d] = run_sum<long long>(heads, lane, o[d]);
+            if (g[u] >= 0 && ((heads >> lane) & 1u))
+                for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g[u] + d], (unsigned long long)o[d]);
+        }
     }
 }
 
-template <typename T>
-__global__ void halo_centre_kernel(const T *__restrict__ pos, int64_t G, double box,
-                                   const unsigned long long *__restrict__ pkey,
+// Per group: count, peak, the centre in units (cen, in [0, 2^32); it holds
+// the peak's coordinates on entry) and in box coordinates (com).
+__global__ void halo_centre_kernel(int64_t G, double box, const unsigned long long *__restrict__ pkey,
                                    const unsigned long long *__restrict__ cnt,
-                                   const unsigned long long *__restrict__ sum,
+                                   const unsigned long long *__restrict__ sum, long long *__restrict__ cen,
                                    int64_t *__restrict__ count, uint32_t *__restrict__ peak, double *__restrict__ com)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long c = cnt[g];
         count[g] = (int64_t)c;
-        const uint32_t p = c ? 0xFFFFFFFFu - (uint32_t)pkey[g] : 0u;
-        peak[g] = p;
+        peak[g] = c ? 0xFFFFFFFFu - (uint32_t)pkey[g] : 0u;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double mean = (double)(long long)sum[3 * g + d] / (double)c * (box / 4294967296.0);
-            double x = c ? coord(pos, (int64_t)p, d) + mean : 0.0;
-            if (x < 0.0) x += box;
+            double u = 0.0;
+            if (c) {
+                u = (double)cen[3 * g + d] + (double)(long long)sum[3 * g + d] / (double)c;
+                if (u < 0.0) u += (double)kUnits;
+                if (u >= (double)kUnits) u -= (double)kUnits;
+            }
+            cen[3 * g + d] = __double2ll_rn(u) & (kUnits - 1);
+            double x = u * (box / (double)kUnits);
             if (x >= box) x -= box;
             com[3 * g + d] = x;
         }
     }
 }
 
+// Largest squared member distance from the centre, in units^2: every
+// wrapped component is at most 2^31, so the sum of three squares fits
+// uint64.
 template <typename T>
 __global__ void halo_radius_kernel(const T *__restrict__ pos, const int32_t *__restrict__ group, int64_t n, int64_t G,
-                                   double box, const double *__restrict__ com, unsigned long long *__restrict__ rbits)
+                                   Scale sc, const long long *__restrict__ cen, unsigned long long *__restrict__ r2max)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        int32_t g = i < n ? group[i] : -1;
-        if (g >= G) g = -1;
-        if (!__any_sync(0xffffffffu, g >= 0)) continue;
-        const uint32_t heads = run_heads((int64_t)g, lane);
-        unsigned long long b = 0;
-        if (g >= 0) {
-            double r2 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
+        int32_t g[kHaloU];
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            g[u] = i < n ? group[i] : -1;
+            if (g[u] >= G) g[u] = -1;
+        }
+        T x[kHaloU][3];
+        long long c[kHaloU][3];
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const double dx = min_image_d(coord(pos, i, d) - com[3 * (int64_t)g + d], box);
-                r2 += dx * dx;
+                x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
+                c[u][d] = g[u] >= 0 ? cen[3 * (int64_t)g[u] + d] : 0;
             }
-            // non-negative doubles order like their bit patterns
-            b = (unsigned long long)__double_as_longlong(sqrt(r2));
         }
-        b = run_max(heads, lane, b);
-        if (g >= 0 && ((heads >> lane) & 1u)) atomicMax(&rbits[g], b);
+#pragma unroll
+        for (int u = 0; u < kHaloU; ++u) {
+            if (!__any_sync(0xffffffffu, g[u] >= 0)) continue;
+            const uint32_t heads = run_heads((int64_t)g[u], lane);
+            unsigned long long b = 0;
+            if (g[u] >= 0) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const long long dx = wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]);
+                    b += (unsigned long long)(dx * dx);
+                }
+            }
+            b = run_max(heads, lane, b);
+            if (g[u] >= 0 && ((heads >> lane) & 1u)) atomicMax(&r2max[g[u]], b);
+        }
     }
 }
 
-__global__ void halo_rmax_kernel(int64_t G, const unsigned long long *__restrict__ rbits, double *__restrict__ rmax)
+__global__ void halo_rmax_kernel(int64_t G, double box, const unsigned long long *__restrict__ r2max,
+                                 double *__restrict__ rmax)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x)
-        rmax[g] = __longlong_as_double((long long)rbits[g]);
+        rmax[g] = sqrt((double)r2max[g]) * (box / (double)kUnits);
 }
 
 template <typename T>
 int halo_stats_t(hop_ctx *c, const T *pos, const float *dens, const int32_t *group, int64_t n, int64_t G,
                  double box, int64_t *count, uint32_t *peak, double *com, double *rmax)
 {
-    // scratch: peak keys, counts, offset sums (3), radius bits
-    char *s = (char *)ctx_buf(c, S_HALO, (size_t)G * 6 * 8);
+    // scratch: peak keys, counts, squared radii, offset sums (3), centres in units (3)
+    char *s = (char *)ctx_buf(c, S_HALO, (size_t)G * 9 * 8);
     if (!s) return HOP_ENOMEM;
-    unsigned long long *pkey = (unsigned long long *)s, *cnt = pkey + G, *rbits = cnt + G, *sum = rbits + G;
+    unsigned long long *pkey = (unsigned long long *)s, *cnt = pkey + G, *r2 = cnt + G, *sum = r2 + G;
+    long long *cen = (long long *)(sum + 3 * G);
     HOP_CUDA(c, cudaMemsetAsync(s, 0, (size_t)G * 6 * 8, c->stream));
+    Scale sc;
+    sc.s = (double)kUnits / box;
+    sc.hi = (float)sc.s;
+    sc.lo = (float)(sc.s - (double)sc.hi);
     halo_peak_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(dens, group, n, G, pkey, cnt, c->d_err);
     HOP_LAUNCH(c);
-    halo_sum_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(pos, group, n, G, box, pkey, sum);
+    halo_peak_pos_kernel<T><<<grid_for(c, G), 256, 0, c->stream>>>(pos, G, sc, pkey, cnt, cen);
     HOP_LAUNCH(c);
-    halo_centre_kernel<T><<<grid_for(c, G), 256, 0, c->stream>>>(pos, G, box, pkey, cnt, sum, count, peak, com);
+    halo_sum_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(pos, group, n, G, sc, cen, sum);
     HOP_LAUNCH(c);
-    halo_radius_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(pos, group, n, G, box, com, rbits);
+    halo_centre_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, box, pkey, cnt, sum, cen, count, peak, com);
     HOP_LAUNCH(c);
-    halo_rmax_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, rbits, rmax);
+    halo_radius_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(pos, group, n, G, sc, cen, r2);
+    HOP_LAUNCH(c);
+    halo_rmax_kernel<<<grid_for(c, G), 256, 0, c->stream>>>(G, box, r2, rmax);
     HOP_LAUNCH(c);
     return HOP_OK;
 }

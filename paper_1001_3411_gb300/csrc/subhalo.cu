@@ -113,31 +113,41 @@ __global__ void sub_compress_kernel(uint32_t *parent, int64_t C)
 // S4: count, density sum and peak key of every component's members.  The
 // sum (fp64 atomics, the slow part) is taken only when the significance
 // cut needs it (sum != nullptr).
+// The per-particle passes take kSubU elements per thread per batch and
+// issue the batch's loads before reducing any of it, so the loads overlap.
+constexpr int kSubU = 4;
+
 __global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc,
-                                    int64_t n, float ds, const uint32_t *__restrict__ parent,
-                                    unsigned long long *__restrict__ cnt, double *__restrict__ sum,
-                                    unsigned long long *__restrict__ pkey)
+                                        int64_t n, float ds, const uint32_t *__restrict__ parent,
+                                        unsigned long long *__restrict__ cnt, double *__restrict__ sum,
+                                        unsigned long long *__restrict__ pkey)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        uint32_t r = kNone;
-        uint64_t k = 0;
-        if (i < n) {
-            k = dkey[i];
-            const uint32_t c = pc[i];
-            if (c != kNone && key_dens(k) >= ds) r = parent[c];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSubU;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kSubU; base < n; base += stride) {
+        uint64_t k[kSubU];
+        uint32_t c[kSubU], r[kSubU];
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            k[u] = i < n ? dkey[i] : 0ull;
+            c[u] = i < n ? pc[i] : kNone;
         }
-        if (!__any_sync(0xffffffffu, r != kNone)) continue;
-        // runs of consecutive lanes in one component: one atomic per run
-        const uint32_t heads = run_heads((int64_t)r, lane);
-        const double s = sum ? run_sum<double>(heads, lane, r != kNone ? (double)key_dens(k) : 0.0) : 0.0;
-        const unsigned long long best = run_max(heads, lane, r != kNone ? k : 0ull);
-        if (r != kNone && ((heads >> lane) & 1u)) {
-            atomicAdd(&cnt[r], (unsigned long long)run_len(heads, lane));
-            if (sum) atomicAdd(&sum[r], s);
-            atomicMax(&pkey[r], best);
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) r[u] = (c[u] != kNone && key_dens(k[u]) >= ds) ? parent[c[u]] : kNone;
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) {
+            if (!__any_sync(0xffffffffu, r[u] != kNone)) continue;
+            // runs of consecutive lanes in one component: one atomic per run
+            const uint32_t heads = run_heads((int64_t)r[u], lane);
+            const double sm =
+                sum ? run_sum<double>(heads, lane, r[u] != kNone ? (double)key_dens(k[u]) : 0.0) : 0.0;
+            const unsigned long long best = run_max(heads, lane, r[u] != kNone ? k[u] : 0ull);
+            if (r[u] != kNone && ((heads >> lane) & 1u)) {
+                atomicAdd(&cnt[r[u]], (unsigned long long)run_len(heads, lane));
+                if (sum) atomicAdd(&sum[r[u]], sm);
+                atomicMax(&pkey[r[u]], best);
+            }
         }
     }
 }
@@ -191,18 +201,26 @@ __global__ void sub_rank_kernel(DevCount Gc, const uint32_t *__restrict__ gv, ui
 }
 
 __global__ void sub_label_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc, int64_t n,
-                             float ds, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ flag,
-                             const uint32_t *__restrict__ rank, int32_t *__restrict__ sub)
+                                 float ds, const uint32_t *__restrict__ parent, const uint32_t *__restrict__ flag,
+                                 const uint32_t *__restrict__ rank, int32_t *__restrict__ sub)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t g = -1;
-        const uint32_t c = pc[i];
-        if (c != kNone && key_dens(dkey[i]) >= ds) {
-            const uint32_t r = parent[c];
-            if (flag[r]) g = (int32_t)rank[r];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSubU;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kSubU; base < n; base += stride) {
+        uint64_t k[kSubU];
+        uint32_t c[kSubU], r[kSubU];
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            k[u] = i < n ? dkey[i] : 0ull;
+            c[u] = i < n ? pc[i] : kNone;
         }
-        sub[i] = g;
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) r[u] = (c[u] != kNone && key_dens(k[u]) >= ds) ? parent[c[u]] : kNone;
+#pragma unroll
+        for (int u = 0; u < kSubU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            if (i < n) sub[i] = (r[u] != kNone && flag[r[u]]) ? (int32_t)rank[r[u]] : -1;
+        }
     }
 }
 
