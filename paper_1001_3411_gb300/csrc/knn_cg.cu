@@ -346,7 +346,7 @@ __device__ __forceinline__ void rows_find(const int *hist, int q, int p, int ran
 #pragma unroll 4
     for (int i = 0; i < PER; ++i) {
 #pragma unroll
-        for (int r = 0; r < P; ++r) mine += h0[i * 32 + r];
+        for (int r = 0; r < P; ++r) mine += h0[i * 32 + ((r + p) & (P - 1))];   // lanes p of a group: distinct banks
     }
     int incl = mine;
 #pragma unroll
@@ -362,7 +362,7 @@ __device__ __forceinline__ void rows_find(const int *hist, int q, int p, int ran
         for (int i = 0; i < PER; ++i) {
             int h = 0;
 #pragma unroll
-            for (int r = 0; r < P; ++r) h += h0[i * 32 + r];
+            for (int r = 0; r < P; ++r) h += h0[i * 32 + ((r + p) & (P - 1))];
             if (cum + h >= rank) {
                 fb = p * PER + i + 1;
                 fbelow = cum;
@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 4) knn_cg_kernel(CgDev a)
 // follow as in the grouped kernel above.
 constexpr int kWqChunk = 4;                 // queries per chunk (the radius is per chunk)
 constexpr int kWqBins = 32;                 // histogram bins per lane row
-constexpr int kWqCells = 256;               // cells of one query's region held at once
+constexpr int kWqCells = 128;               // cells of one query's region held at once
 
 struct WqSmem {
     static constexpr size_t cra = 0;                                   // kWqCells range starts
@@ -857,8 +857,10 @@ __device__ __forceinline__ void wq_rows_find(const int *hist, int lane, int rank
                                              int &tot)
 {
     int mine = 0;
+    // lane b reads row r at column (r + b) mod 32, so the 32 lanes of each
+    // load hit 32 different banks
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + r];
+    for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + ((r + lane) & 31)];
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -999,34 +1001,112 @@ __device__ __forceinline__ void wq_visit(const float4 *__restrict__ spos, const 
 
 // The n_out nearest of a warp's list when more than kOC entries lie up to
 // the n_out-th bin (long Nhop lists, ties): each entry up to edge_o is
-// ranked by (d^2, original index) against the whole list.  Out of line: the
-// common path gathers at most kOC entries instead.
+// ranked by (d^2, original index) against the whole list.  A lane ranks
+// four entries (e, e + 32, e + 64, e + 96) in one pass over the list;
+// equal distances are ordered by original index in a second pass, taken
+// only when some entry has one.  Out of line: the common path gathers at
+// most kOC entries instead.
 __device__ __noinline__ void wq_rank_in_list(const float *Ld, const uint32_t *Ls, int cnt, float edge_o, int n_out,
                                              const float4 *__restrict__ spos, uint32_t *row, int lane)
 {
-    for (int e = lane; e < cnt; e += 32) {
-        const float v = Ld[e];
-        if (!(v <= edge_o)) continue;
-        const uint32_t se = Ls[e];
-        uint32_t oe = 0xffffffffu;
-        int rank = 0;
+    constexpr int B = 4;
+    for (int e0 = 0; e0 < cnt; e0 += 32 * B) {
+        float v[B];
+        int rank[B], eq[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int e = e0 + 32 * j + lane;
+            v[j] = e < cnt ? Ld[e] : INFINITY;
+            if (!(v[j] <= edge_o)) v[j] = -1.f;   // not ranked; compares as nothing below it
+            rank[j] = 0;
+            eq[j] = 0;
+        }
         for (int f = 0; f < cnt; ++f) {
             const float u = Ld[f];
-            if (u < v) {
-                ++rank;
-                continue;
-            }
-            if (u == v && f != e) {
-                if (oe == 0xffffffffu) oe = __float_as_uint(spos[se].w);
-                rank += __float_as_uint(spos[Ls[f]].w) < oe;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                rank[j] += u < v[j];
+                eq[j] += u == v[j];
             }
         }
-        if (rank < n_out) row[rank] = se;
+        bool tie = false;
+#pragma unroll
+        for (int j = 0; j < B; ++j) tie |= v[j] >= 0.f && eq[j] > 1;
+        if (__any_sync(kAll, tie)) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int e = e0 + 32 * j + lane;
+                if (!(v[j] >= 0.f && eq[j] > 1)) continue;
+                const uint32_t oe = __float_as_uint(spos[Ls[e]].w);
+                for (int f = 0; f < cnt; ++f)
+                    if (f != e && Ld[f] == v[j]) rank[j] += __float_as_uint(spos[Ls[f]].w) < oe;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int e = e0 + 32 * j + lane;
+            if (v[j] >= 0.f && rank[j] < n_out) row[rank[j]] = Ls[e];
+        }
     }
 }
 
+// Bitonic sort across the warp, one element per lane, ascending by lane.
+__device__ __forceinline__ float warp_sort32(float v, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(kAll, v, j);
+            v = (((lane & j) == 0) == ((lane & k) == 0)) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return v;
+}
+
+__device__ __forceinline__ void warp_sort32(unsigned long long &key, uint32_t &pay, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(kAll, key, j);
+            const uint32_t op = __shfl_xor_sync(kAll, pay, j);
+            const bool take = (((lane & j) == 0) == ((lane & k) == 0)) ? o < key : o > key;
+            if (take) {
+                key = o;
+                pay = op;
+            }
+        }
+    }
+}
+
+// Exact rank-th smallest d^2 of the warp's list, whose entries in (lo, ...]
+// hold it with `below` smaller entries outside: up to 32 such entries (the
+// k-th bin) are sorted across the warp; more go through the radix descent.
+__device__ __forceinline__ float wq_list_kth(const float *Ld, int cnt, float lo, int below, int upto, int rank,
+                                             float *kd, int lane, uint32_t lt)
+{
+    if (upto - below > 32)
+        return list_kth_deep<32>(true, Ld, cnt, cnt, lo, below, rank, (int *)kd, lane);
+    int nk = 0;
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        const float v = e < cnt ? Ld[e] : 0.f;
+        const bool in = e < cnt && v > lo;
+        const uint32_t bal = __ballot_sync(kAll, in);
+        const int pos = nk + __popc(bal & lt);
+        if (in && pos < 32) kd[pos] = v;
+        nk += __popc(bal);
+    }
+    __syncwarp();
+    const float mine = lane < nk ? kd[lane] : INFINITY;
+    const float sorted = warp_sort32(mine, lane);
+    return __shfl_sync(kAll, sorted, rank - below - 1);
+}
+
 template <bool SEG>
-__global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
+__global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
 {
     using L = WqSmem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1296,7 +1376,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
                 continue;
             }
             // ------------- selection (the list is in Ld / Ls)
-            const float vk = list_kth<32>(true, Ld, cnt, cnt, lo_k, below_k, upto_k, k, kd, lane, kAll, lt);
+            const float vk = wq_list_kth(Ld, cnt, lo_k, below_k, upto_k, k, kd, lane, lt);
             unsigned long long wsum = 0;
             const float rk = sqrtf(vk);
             const float inv_h = vk > 0.f ? 2.f / rk : 0.f;
@@ -1310,43 +1390,38 @@ __global__ void __launch_bounds__(kCgWarps * 32, 6) knn_wq_kernel(CgDev a)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(kAll, wsum, o);
             if (n_out > 0) {
-                if (upto_o <= kOC) {
+                if (upto_o <= 32) {
+                    // at most 32 entries up to the n_out-th bin: one per lane,
+                    // sorted across the warp by (d^2, original index)
                     int no = 0;
                     for (int e0 = 0; e0 < cnt; e0 += 32) {
                         const int e = e0 + lane;
-                        float v = 0.f;
-                        uint32_t sv = 0;
-                        bool in = false;
-                        if (e < cnt) {
-                            v = Ld[e];
-                            sv = Ls[e];
-                            in = v <= edge_o;
-                        }
+                        const float v = e < cnt ? Ld[e] : 0.f;
+                        const bool in = e < cnt && v <= edge_o;
                         const uint32_t bal = __ballot_sync(kAll, in);
                         const int pos = no + __popc(bal & lt);
-                        if (in && pos < kOC) {
+                        if (in && pos < 32) {
                             od[pos] = v;
-                            os[pos] = sv;
+                            os[pos] = Ls[e];
                         }
                         no += __popc(bal);
                     }
                     __syncwarp();
-                    const int ng = min(no, kOC);
-                    if (lane < ng) {
-                        const float v = od[lane];
-                        const uint32_t se = os[lane];
-                        uint32_t oe = 0xffffffffu;
-                        int rank = 0;
-                        for (int f = 0; f < ng; ++f) {
-                            const float u = od[f];
-                            rank += u < v;
-                            if (u == v && f != lane) {
-                                if (oe == 0xffffffffu) oe = __float_as_uint(a.spos[se].w);
-                                rank += __float_as_uint(a.spos[os[f]].w) < oe;
-                            }
-                        }
-                        if (rank < n_out) a.nbr_s[(size_t)sq * a.ld_out + rank] = se;
+                    // sorted by (d^2, sorted index) first; equal distances, if
+                    // any, are sorted again by original index
+                    unsigned long long key = ~0ull;
+                    uint32_t pay = 0u;
+                    if (lane < no) {
+                        pay = os[lane];
+                        key = ((unsigned long long)__float_as_uint(od[lane]) << 32) | pay;
                     }
+                    warp_sort32(key, pay, lane);
+                    const unsigned long long prev = __shfl_up_sync(kAll, key, 1);
+                    if (__any_sync(kAll, lane > 0 && lane < no && (prev >> 32) == (key >> 32))) {
+                        if (lane < no) key = (key & 0xffffffff00000000ull) | __float_as_uint(a.spos[pay].w);
+                        warp_sort32(key, pay, lane);
+                    }
+                    if (lane < min(no, n_out)) a.nbr_s[(size_t)sq * a.ld_out + lane] = pay;
                 } else {
                     wq_rank_in_list(Ld, Ls, cnt, edge_o, n_out, a.spos, a.nbr_s + (size_t)sq * a.ld_out, lane);
                 }
