@@ -151,7 +151,7 @@ __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__rest
             for (int d = 0; d < 3; ++d)
                 o[d] = g[u] >= 0 ? wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]) : 0;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) o[d] = run_sum<long long>(heads, lane, o[d]);
+            for (int d = 0; d < 3; ++d) o[d] = run_sum_i42(heads, lane, o[d]);   // |o| <= 2^31
             if (g[u] >= 0 && ((heads >> lane) & 1u))
                 for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g[u] + d], (unsigned long long)o[d]);
         }

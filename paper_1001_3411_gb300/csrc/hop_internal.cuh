@@ -293,6 +293,14 @@ template <typename V> __device__ __forceinline__ V run_sum(uint32_t heads, int l
 }
 __device__ __forceinline__ unsigned long long run_max(uint32_t heads, int lane, unsigned long long v)
 {
+    if (heads == 1u) {
+        // the warp is one run: two 32-bit reductions (high half, then the
+        // low half among the lanes holding the highest)
+        const unsigned hi = (unsigned)(v >> 32);
+        const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? (unsigned)v : 0u);
+        return ((unsigned long long)mh << 32) | ml;
+    }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const unsigned long long o = __shfl_down_sync(0xffffffffu, v, d);
@@ -300,6 +308,15 @@ __device__ __forceinline__ unsigned long long run_max(uint32_t heads, int lane, 
         if (lane + d < 32 && (heads & between) == 0 && o > v) v = o;
     }
     return v;
+}
+// run_sum of integers below 2^42 in magnitude; a warp that is one run sums
+// the value's high part (v >> 16) and low 16 bits in two 32-bit reductions.
+__device__ __forceinline__ long long run_sum_i42(uint32_t heads, int lane, long long v)
+{
+    if (heads == 1u)
+        return ((long long)__reduce_add_sync(0xffffffffu, (int)(v >> 16)) << 16) +
+               (long long)__reduce_add_sync(0xffffffffu, (unsigned)v & 0xffffu);
+    return run_sum<long long>(heads, lane, v);
 }
 // Lanes in the run that starts at this head lane.
 __device__ __forceinline__ int run_len(uint32_t heads, int lane)

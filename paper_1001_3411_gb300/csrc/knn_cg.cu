@@ -828,39 +828,51 @@ __global__ void __launch_bounds__(kCgWarps * 32, 4) knn_cg_kernel(CgDev a)
 // list, the exact Ndens-th distance, the density and the n_out nearest
 // follow as in the grouped kernel above.
 constexpr int kWqChunk = 4;                 // queries per chunk (the radius is per chunk)
-constexpr int kWqBins = 32;                 // histogram bins per lane row
+constexpr int kWqBins = 16;                 // histogram bins per lane row (quarter octaves of d^2)
+constexpr int kWqBinsLog = 4;
+constexpr int kWqGather = 256;              // entries the count scan keeps, so the gather scan can be skipped
 constexpr int kWqCells = 128;               // cells of one query's region held at once
 
+// Shared memory of one warp, byte offsets.  The histogram rows (count
+// scans) share their space with the small selection lists (kd, od, os);
+// the count scan's list (gd, gs: kWqGather entries) shares its space with
+// the gather scan's list (Ld, Ls: capq entries), which is only used when
+// the first is too short.
 struct WqSmem {
     static constexpr size_t cra = 0;                                   // kWqCells range starts
     static constexpr size_t cln = cra + kWqCells * 4;                  // kWqCells range lengths
     static constexpr size_t cmd = cln + kWqCells * 4;                  // kWqCells min distance^2 to the query
     static constexpr size_t cpre = cmd + kWqCells * 4;                 // kWqCells + 1 prefix offsets
-    static constexpr size_t uni = (cpre + (kWqCells + 1) * 4 + 15) & ~size_t(15);
+    static constexpr size_t hist = (cpre + (kWqCells + 1) * 4 + 15) & ~size_t(15);
     static constexpr size_t hist_bytes = (size_t)kWqBins * 32 * 4;
-    __host__ __device__ static size_t ls(int capq) { return uni + (size_t)capq * 4; }
-    __host__ __device__ static size_t kd(int capq) { return uni + (size_t)capq * 8; }
-    __host__ __device__ static size_t od(int capq) { return kd(capq) + kKC * 4; }
-    __host__ __device__ static size_t os(int capq) { return od(capq) + kOC * 4; }
+    static constexpr size_t kd = hist;
+    static constexpr size_t od = kd + kKC * 4;
+    static constexpr size_t os = od + kOC * 4;
+    static_assert(kKC * 4 + kOC * 8 <= hist_bytes, "selection lists fit the histogram rows");
+    static constexpr size_t gd = hist + hist_bytes;
+    static constexpr size_t gs = gd + kWqGather * 4;
+    __host__ __device__ static size_t ls(int capq) { return gd + (size_t)capq * 4; }
     __host__ __device__ static size_t total(int capq)
     {
-        const size_t lists = os(capq) + kOC * 4 - uni;
-        const size_t u = lists > hist_bytes ? lists : hist_bytes;
-        return (uni + u + 15) & ~size_t(15);
+        const size_t g = kWqGather * 8 > (size_t)capq * 8 ? kWqGather * 8 : (size_t)capq * 8;
+        return (gd + g + 15) & ~size_t(15);
     }
 };
 
-// Bin of the rank-th entry over the 32 histogram rows (lane b sums bin b):
+// Bin of the rank-th entry over the histogram rows (lane b < kWqBins sums
+// bin b over the 32 lanes' columns):
 // the bin (-1 if fewer entries), the entries below it and up to it, and the
 // total.  Uniform over the warp.
 __device__ __forceinline__ void wq_rows_find(const int *hist, int lane, int rank, int &bin, int &below, int &upto,
                                              int &tot)
 {
     int mine = 0;
-    // lane b reads row r at column (r + b) mod 32, so the 32 lanes of each
-    // load hit 32 different banks
+    // lane b reads column c of its row at (c + b) mod 32, so the lanes of
+    // each load hit different banks
+    if (lane < kWqBins) {
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + ((r + lane) & 31)];
+        for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + ((r + lane) & 31)];
+    }
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1119,12 +1131,12 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
     uint32_t *cln = (uint32_t *)(wb + L::cln);
     float *cmd = (float *)(wb + L::cmd);
     uint32_t *cpre = (uint32_t *)(wb + L::cpre);
-    int *hist = (int *)(wb + L::uni);
-    float *Ld = (float *)(wb + L::uni);
-    uint32_t *Ls = (uint32_t *)(wb + L::ls(capq));
-    float *kd = (float *)(wb + L::kd(capq));
-    float *od = (float *)(wb + L::od(capq));
-    uint32_t *os = (uint32_t *)(wb + L::os(capq));
+    int *hist = (int *)(wb + L::hist);
+    float *gd = (float *)(wb + L::gd);
+    uint32_t *gs = (uint32_t *)(wb + L::gs);
+    float *kd = (float *)(wb + L::kd);
+    float *od = (float *)(wb + L::od);
+    uint32_t *os = (uint32_t *)(wb + L::os);
     const int k = a.k;
     const int n_out = a.nbr_s ? a.n_out : 0;
     const int cpr = min(max(a.cpr, 1), 3);
@@ -1186,6 +1198,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
             int bk = -1, below_k = 0, upto_k = 0, bk0 = -1, bo = -1, upto_o = 0;
             float edge_o = -1.f;
             bool fresh = true;   // the region must be (re)built for R
+            int gn = 0;          // entries within R kept by the certifying count scan
             for (;;) {
                 if (fresh) {
                     ++search_acc;
@@ -1232,9 +1245,12 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     const int base = top - (kWqBins - 1);
                     int *hcol = hist + lane;
                     cand_acc += total;
-                    wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t, bool valid) {
-                        if (!valid) return;
-                        float dx, dy, dz;
+                    // until certified, the particles within R are also kept
+                    // (up to kWqGather), which spares the gather scan
+                    const bool keep_list = !certified;
+                    if (keep_list) gn = 0;
+                    wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t s, bool valid) {
+                        float dx = 0.f, dy = 0.f, dz = 0.f;
                         if (full) {
                             dx = wrapdiff(v.x, rqx, box, half);
                             dy = wrapdiff(v.y, rqy, box, half);
@@ -1249,9 +1265,19 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                             dz = v.z - qz;
                         }
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (d2 <= tauA) {
+                        const bool in = valid && d2 <= tauA;
+                        if (in) {
                             const int b = max((int)(__float_as_uint(d2) >> shift) - base, 0);
                             hcol[b * 32] += 1;
+                        }
+                        if (keep_list) {
+                            const uint32_t bal = __ballot_sync(kAll, in);
+                            const int pos = gn + __popc(bal & lt);
+                            if (in && pos < kWqGather) {
+                                gd[pos] = d2;
+                                gs[pos] = s;
+                            }
+                            gn += __popc(bal);
                         }
                     });
                 }
@@ -1278,7 +1304,9 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                         edge_o = bin_edge(top - (kWqBins - 1), shift, bo);
                     }
                 }
-                if (upto_k <= capq) break;
+                // a complete list of the particles within R: the gather scan
+                // is not needed, nor a finer count of a crowded bin
+                if (gn <= kWqGather || upto_k <= capq) break;
                 // a crowded Ndens-th bin: count again in a finer (or lower) window
                 if (++refines > kRefine) {
                     if (lane == 0) atomicOr(a.err, kErrDegenerate);
@@ -1290,7 +1318,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     tauA = fminf(tauA, bin_edge(base, shift, 0));
                     top -= kWqBins - 1;
                 } else if (shift > 0) {
-                    const int ns = max(shift - 5, 0), d = shift - ns;
+                    const int ns = max(shift - kWqBinsLog, 0), d = shift - ns;
                     tauA = fminf(tauA, bin_edge(base, shift, bk));
                     top = ((base + bk) << d) | ((1 << d) - 1);
                     shift = ns;
@@ -1310,6 +1338,35 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
             }
             edge_o = fminf(edge_o, edge_k);
 
+            const bool listed = gn <= kWqGather;
+            // the list: the count scan's (gd, gs), or the gather scan's, in
+            // the same space (Ld = gd, Ls after capq entries)
+            float *Ld = gd;
+            uint32_t *Ls = listed ? gs : (uint32_t *)(wb + L::ls(capq));
+            int cnt = 0;
+            if (listed) {
+                // ------------- the count scan's list, cut to the Ndens-th bin
+                for (int e0 = 0; e0 < gn; e0 += 32) {
+                    const int e = e0 + lane;
+                    float v = 0.f;
+                    uint32_t sv = 0;
+                    bool keep = false;
+                    if (e < gn) {
+                        v = gd[e];
+                        sv = gs[e];
+                        keep = v <= edge_k;
+                    }
+                    const uint32_t bal = __ballot_sync(kAll, keep);
+                    const int pos = cnt + __popc(bal & lt);
+                    __syncwarp();
+                    if (keep) {
+                        gd[pos] = v;
+                        gs[pos] = sv;
+                    }
+                    cnt += __popc(bal);
+                    __syncwarp();
+                }
+            } else {
             // ------------- scan B: gather every entry up to the Ndens-th bin,
             // from the cells that meet its ball
             if (!full) {
@@ -1337,7 +1394,6 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                 nc = keep_n;
                 total = wq_prefix(cln, cpre, nc, lane);
             }
-            int cnt = 0;
             {
                 cand_acc += total;
                 wq_visit(a.spos, cra, cpre, nc, total, lane, [&](const float4 &v, uint32_t s, bool valid) {
@@ -1368,6 +1424,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     }
                     cnt += __popc(bal);
                 });
+            }
             }
             __syncwarp();
             if (cnt != upto_k) {

@@ -10,8 +10,8 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 4096
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 4096
+constexpr int kSortItems = 12;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 3072
 constexpr int kSortWarps = kSortThreads / 32;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -105,7 +105,7 @@ __global__ void scan_apply_kernel(const uint32_t *__restrict__ in, uint32_t *__r
 //
 // Stable LSD radix sort, 8 bits per pass, one read and one write of the
 // (key, value) pairs per pass.  One kernel counts the digits of every pass
-// up front; a pass then needs, for each tile of 4096 items and each digit,
+// up front; a pass then needs, for each tile of 3072 items and each digit,
 // how many items of that digit the earlier tiles hold.  Tiles are taken in
 // input order from a counter, so every earlier tile is already running: a
 // tile publishes its own digit counts, then walks back over its
@@ -169,8 +169,8 @@ __global__ void radix_digits_kernel(const uint64_t *__restrict__ keys, DevCount 
 }
 
 // One pass.  A block takes the next tile from *tile_ctr; warp w ranks its
-// 512 items (16 rounds of 32 consecutive items, input order) per digit with
-// match/popc and its own digit counters; a scan over (digit, warp) gives
+// 384 items (12 rounds of 32 consecutive items, input order) per digit with
+// ballots/popc and its own digit counters; a scan over (digit, warp) gives
 // each item its position in the tile sorted by digit; the look-back gives
 // each digit's global position; the tile is rebuilt in shared memory in
 // digit order and written out in order, so each digit's run goes to
@@ -178,7 +178,7 @@ __global__ void radix_digits_kernel(const uint64_t *__restrict__ keys, DevCount 
 // *tile_ctr are zero on entry.
 constexpr int kLsSmem = kSortWarps * 256 * 4 + 256 * 4 + kSortTile * 12;
 
-__global__ void __launch_bounds__(kSortThreads, 2) radix_onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 3) radix_onesweep_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint64_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, DevCount nc, int shift, const uint32_t *__restrict__ digit_count,
     uint64_t *__restrict__ status, uint32_t *__restrict__ tile_ctr, uint32_t *__restrict__ err)
@@ -217,7 +217,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) radix_onesweep_kernel(
         const int64_t i = tile + (int64_t)warp * (32 * kSortItems) + r * 32 + lane;
         const bool valid = i < n;
         const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit: eight ballots, one per digit bit (a
+        // warp match costs more here)
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t vb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? vb : ~vb;
+        }
         const uint32_t leader = __ffs(peers) - 1;
         uint32_t prior = 0;
         if (valid && lane == leader) {
