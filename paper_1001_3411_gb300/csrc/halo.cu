@@ -17,12 +17,12 @@
 // arithmetic runs in fp64 (GB300's fp64 rate is a small fraction of its
 // fp32 rate); the split scale makes the fp32 product exact enough.
 //
-// Three grid-stride passes over the particles, each HBM-bound: peak keys
-// and counts, offset sums, then the radii; between them, per group, the
-// peak's coordinates and the centre.  A warp
-// reduces each run of consecutive lanes holding the same group with a
-// segmented shuffle scan (five steps), so one atomic per run reaches
-// memory; members of a halo are mostly consecutive in the input.
+// Three passes over the particles, each HBM-bound: peak keys and counts,
+// offset sums, then the radii; between them, per group, the peak's
+// coordinates and the centre.  A warp reduces each run of consecutive lanes
+// holding the same group with a segmented shuffle scan (five steps) and
+// carries its last run on to the next 32 particles, so a halo's members,
+// mostly consecutive in the input, cost few atomics.
 #include "hop_internal.cuh"
 
 #include <algorithm>
@@ -61,44 +61,83 @@ struct Scale {
     float hi, lo;      // s split into two floats
 };
 
-// Each pass takes the particles in batches of kHaloU blocks' width per
-// block: a thread loads its kHaloU elements' group ids (and the data they
-// need) before any of them is reduced, so the loads of a batch overlap.
+// Each pass gives every warp spans of kHaloSpan consecutive particles, 32
+// per step, loading kHaloU steps before reducing any of them.  Runs of equal
+// group ids are reduced across the warp; every complete run goes to memory
+// with one atomic, and the warp's last run is carried into the next step
+// (members of a halo are mostly consecutive, so a large halo costs one
+// atomic per span rather than one per step).
 constexpr int kHaloU = 4;
+constexpr int kHaloSteps = 32;
+constexpr int kHaloSpan = 32 * kHaloSteps;
+
+struct WarpSpan {
+    int64_t w, nw;
+    __device__ WarpSpan()
+    {
+        w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    }
+};
+
+__device__ __forceinline__ int last_head(uint32_t heads) { return 31 - __clz(heads); }
 
 __global__ void halo_peak_kernel(const float *__restrict__ dens, const int32_t *__restrict__ group, int64_t n,
                                  int64_t G, unsigned long long *__restrict__ pkey,
                                  unsigned long long *__restrict__ count, uint32_t *__restrict__ err)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
-        int32_t g[kHaloU];
-        float dv[kHaloU];
+    const WarpSpan ws;
+    for (int64_t w0 = ws.w * kHaloSpan; w0 < n; w0 += ws.nw * kHaloSpan) {
+        int32_t cg = -1;                      // the carried run: group, best key, length
+        unsigned long long cbest = 0, ccnt = 0;
+        for (int t = 0; t < kHaloSteps; t += kHaloU) {
+            int32_t g[kHaloU];
+            float dv[kHaloU];
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-            g[u] = i < n ? group[i] : -1;
-            dv[u] = i < n ? dens[i] : 0.f;
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
+                g[u] = i < n ? group[i] : -1;
+                dv[u] = i < n ? dens[i] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
+                int32_t gg = g[u];
+                if (gg >= G) {
+                    atomicOr(err, kErrBadIndex);
+                    gg = -1;
+                }
+                if (!__any_sync(0xffffffffu, gg >= 0)) continue;
+                const uint32_t heads = run_heads((int64_t)gg, lane);
+                const unsigned long long key =
+                    gg >= 0 ? ((unsigned long long)__float_as_uint(dv[u]) << 32) |
+                                  (unsigned long long)(0xFFFFFFFFu - (uint32_t)i)
+                            : 0ull;
+                unsigned long long best = run_max(heads, lane, key);
+                unsigned long long len = (unsigned long long)run_len(heads, lane);
+                if (lane == 0 && cg >= 0) {
+                    if (gg == cg) {
+                        best = best > cbest ? best : cbest;
+                        len += ccnt;
+                    } else {
+                        atomicMax(&pkey[cg], cbest);
+                        atomicAdd(&count[cg], ccnt);
+                    }
+                }
+                const int last = last_head(heads);
+                if (gg >= 0 && ((heads >> lane) & 1u) && lane != last) {
+                    atomicMax(&pkey[gg], best);
+                    atomicAdd(&count[gg], len);
+                }
+                cg = __shfl_sync(0xffffffffu, gg, last);
+                cbest = __shfl_sync(0xffffffffu, best, last);
+                ccnt = __shfl_sync(0xffffffffu, len, last);
+            }
         }
-#pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-            int32_t gg = g[u];
-            if (gg >= G) {
-                atomicOr(err, kErrBadIndex);
-                gg = -1;
-            }
-            if (!__any_sync(0xffffffffu, gg >= 0)) continue;
-            const uint32_t heads = run_heads((int64_t)gg, lane);
-            const unsigned long long key =
-                gg >= 0 ? ((unsigned long long)__float_as_uint(dv[u]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i)
-                        : 0ull;
-            const unsigned long long best = run_max(heads, lane, key);
-            if (gg >= 0 && ((heads >> lane) & 1u)) {
-                atomicMax(&pkey[gg], best);
-                atomicAdd(&count[gg], (unsigned long long)run_len(heads, lane));
-            }
+        if (lane == 0 && cg >= 0) {
+            atomicMax(&pkey[cg], cbest);
+            atomicAdd(&count[cg], ccnt);
         }
     }
 }
@@ -122,39 +161,61 @@ __global__ void halo_sum_kernel(const T *__restrict__ pos, const int32_t *__rest
                                 Scale sc, const long long *__restrict__ xp, unsigned long long *__restrict__ sum)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
-        int32_t g[kHaloU];
+    const WarpSpan ws;
+    for (int64_t w0 = ws.w * kHaloSpan; w0 < n; w0 += ws.nw * kHaloSpan) {
+        int32_t cg = -1;
+        long long cs[3] = {0, 0, 0};
+        for (int t = 0; t < kHaloSteps; t += kHaloU) {
+            int32_t g[kHaloU];
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-            g[u] = i < n ? group[i] : -1;
-            if (g[u] >= G) g[u] = -1;
-        }
-        T x[kHaloU][3];
-        long long c[kHaloU][3];
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
+                g[u] = i < n ? group[i] : -1;
+                if (g[u] >= G) g[u] = -1;
+            }
+            T x[kHaloU][3];
+            long long c[kHaloU][3];
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
-                c[u][d] = g[u] >= 0 ? xp[3 * (int64_t)g[u] + d] : 0;
+                for (int d = 0; d < 3; ++d) {
+                    x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
+                    c[u][d] = g[u] >= 0 ? xp[3 * (int64_t)g[u] + d] : 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kHaloU; ++u) {
+                const int32_t gg = g[u];
+                if (!__any_sync(0xffffffffu, gg >= 0)) continue;
+                const uint32_t heads = run_heads((int64_t)gg, lane);
+                long long o[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    o[d] = gg >= 0 ? wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]) : 0;
+                    o[d] = run_sum_i42(heads, lane, o[d]);   // |o| <= 2^31
+                }
+                if (lane == 0 && cg >= 0) {
+                    if (gg == cg) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) o[d] += cs[d];
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)cg + d], (unsigned long long)cs[d]);
+                    }
+                }
+                const int last = last_head(heads);
+                if (gg >= 0 && ((heads >> lane) & 1u) && lane != last)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)gg + d], (unsigned long long)o[d]);
+                cg = __shfl_sync(0xffffffffu, gg, last);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) cs[d] = __shfl_sync(0xffffffffu, o[d], last);
             }
         }
+        if (lane == 0 && cg >= 0)
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            if (!__any_sync(0xffffffffu, g[u] >= 0)) continue;
-            const uint32_t heads = run_heads((int64_t)g[u], lane);
-            long long o[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                o[d] = g[u] >= 0 ? wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]) : 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) o[d] = run_sum_i42(heads, lane, o[d]);   // |o| <= 2^31
-            if (g[u] >= 0 && ((heads >> lane) & 1u))
-                for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)g[u] + d], (unsigned long long)o[d]);
-        }
+            for (int d = 0; d < 3; ++d) atomicAdd(&sum[3 * (int64_t)cg + d], (unsigned long long)cs[d]);
     }
 }
 
@@ -194,41 +255,54 @@ __global__ void halo_radius_kernel(const T *__restrict__ pos, const int32_t *__r
                                    Scale sc, const long long *__restrict__ cen, unsigned long long *__restrict__ r2max)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHaloU;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kHaloU; base < n; base += stride) {
-        int32_t g[kHaloU];
+    const WarpSpan ws;
+    for (int64_t w0 = ws.w * kHaloSpan; w0 < n; w0 += ws.nw * kHaloSpan) {
+        int32_t cg = -1;
+        unsigned long long cb = 0;
+        for (int t = 0; t < kHaloSteps; t += kHaloU) {
+            int32_t g[kHaloU];
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-            g[u] = i < n ? group[i] : -1;
-            if (g[u] >= G) g[u] = -1;
-        }
-        T x[kHaloU][3];
-        long long c[kHaloU][3];
-#pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
-                c[u][d] = g[u] >= 0 ? cen[3 * (int64_t)g[u] + d] : 0;
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
+                g[u] = i < n ? group[i] : -1;
+                if (g[u] >= G) g[u] = -1;
             }
-        }
+            T x[kHaloU][3];
+            long long c[kHaloU][3];
 #pragma unroll
-        for (int u = 0; u < kHaloU; ++u) {
-            if (!__any_sync(0xffffffffu, g[u] >= 0)) continue;
-            const uint32_t heads = run_heads((int64_t)g[u], lane);
-            unsigned long long b = 0;
-            if (g[u] >= 0) {
+            for (int u = 0; u < kHaloU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const long long dx = wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]);
-                    b += (unsigned long long)(dx * dx);
+                    x[u][d] = g[u] >= 0 ? pos[3 * i + d] : T(0);
+                    c[u][d] = g[u] >= 0 ? cen[3 * (int64_t)g[u] + d] : 0;
                 }
             }
-            b = run_max(heads, lane, b);
-            if (g[u] >= 0 && ((heads >> lane) & 1u)) atomicMax(&r2max[g[u]], b);
+#pragma unroll
+            for (int u = 0; u < kHaloU; ++u) {
+                const int32_t gg = g[u];
+                if (!__any_sync(0xffffffffu, gg >= 0)) continue;
+                const uint32_t heads = run_heads((int64_t)gg, lane);
+                unsigned long long b = 0;
+                if (gg >= 0) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const long long dx = wrap_units(fixed_of(x[u][d], sc.hi, sc.lo, sc.s) - c[u][d]);
+                        b += (unsigned long long)(dx * dx);
+                    }
+                }
+                b = run_max(heads, lane, b);
+                if (lane == 0 && cg >= 0) {
+                    if (gg == cg) b = b > cb ? b : cb;
+                    else atomicMax(&r2max[cg], cb);
+                }
+                const int last = last_head(heads);
+                if (gg >= 0 && ((heads >> lane) & 1u) && lane != last) atomicMax(&r2max[gg], b);
+                cg = __shfl_sync(0xffffffffu, gg, last);
+                cb = __shfl_sync(0xffffffffu, b, last);
+            }
         }
+        if (lane == 0 && cg >= 0) atomicMax(&r2max[cg], cb);
     }
 }
 

@@ -115,7 +115,12 @@ __global__ void sub_compress_kernel(uint32_t *parent, int64_t C)
 // cut needs it (sum != nullptr).
 // The per-particle passes take kSubU elements per thread per batch and
 // issue the batch's loads before reducing any of it, so the loads overlap.
+// The member pass gives every warp spans of consecutive particles and
+// carries its last run of one component on to the next 32 (as the halo
+// statistics do), so a large component costs one atomic per span.
 constexpr int kSubU = 4;
+constexpr int kSubSteps = 32;
+constexpr int kSubSpan = 32 * kSubSteps;
 
 __global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const uint32_t *__restrict__ pc,
                                         int64_t n, float ds, const uint32_t *__restrict__ parent,
@@ -123,35 +128,63 @@ __global__ void sub_member_stats_kernel(const uint64_t *__restrict__ dkey, const
                                         unsigned long long *__restrict__ pkey)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kSubU;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kSubU; base < n; base += stride) {
-        uint64_t k[kSubU];
-        uint32_t c[kSubU], r[kSubU];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = w * kSubSpan; w0 < n; w0 += nw * kSubSpan) {
+        uint32_t cr = kNone;                  // the carried run: component, count, sum, best key
+        unsigned long long cc = 0, cb = 0;
+        double csum = 0.0;
+        for (int t = 0; t < kSubSteps; t += kSubU) {
+            uint64_t k[kSubU];
+            uint32_t c[kSubU], r[kSubU];
 #pragma unroll
-        for (int u = 0; u < kSubU; ++u) {
-            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
-            k[u] = i < n ? dkey[i] : 0ull;
-            c[u] = i < n ? pc[i] : kNone;
-        }
-#pragma unroll
-        for (int u = 0; u < kSubU; ++u) r[u] = (c[u] != kNone && key_dens(k[u]) >= ds) ? parent[c[u]] : kNone;
-#pragma unroll
-        for (int u = 0; u < kSubU; ++u) {
-            if (!__any_sync(0xffffffffu, r[u] != kNone)) continue;
-            // runs of consecutive lanes in one component: one atomic per run
-            const uint32_t heads = run_heads((int64_t)r[u], lane);
-            const double sm =
-                sum ? run_sum<double>(heads, lane, r[u] != kNone ? (double)key_dens(k[u]) : 0.0) : 0.0;
-            const unsigned long long best = run_max(heads, lane, r[u] != kNone ? k[u] : 0ull);
-            if (r[u] != kNone && ((heads >> lane) & 1u)) {
-                atomicAdd(&cnt[r[u]], (unsigned long long)run_len(heads, lane));
-                if (sum) atomicAdd(&sum[r[u]], sm);
-                atomicMax(&pkey[r[u]], best);
+            for (int u = 0; u < kSubU; ++u) {
+                const int64_t i = w0 + (int64_t)(t + u) * 32 + lane;
+                k[u] = i < n ? dkey[i] : 0ull;
+                c[u] = i < n ? pc[i] : kNone;
             }
+#pragma unroll
+            for (int u = 0; u < kSubU; ++u)
+                r[u] = (c[u] != kNone && key_dens(k[u]) >= ds) ? parent[c[u]] : kNone;
+#pragma unroll
+            for (int u = 0; u < kSubU; ++u) {
+                const uint32_t rr = r[u];
+                if (!__any_sync(0xffffffffu, rr != kNone)) continue;
+                // runs of consecutive lanes in one component
+                const uint32_t heads = run_heads((int64_t)rr, lane);
+                double sm = sum ? run_sum<double>(heads, lane, rr != kNone ? (double)key_dens(k[u]) : 0.0) : 0.0;
+                unsigned long long best = run_max(heads, lane, rr != kNone ? k[u] : 0ull);
+                unsigned long long len = (unsigned long long)run_len(heads, lane);
+                if (lane == 0 && cr != kNone) {
+                    if (rr == cr) {
+                        len += cc;
+                        sm += csum;
+                        best = best > cb ? best : cb;
+                    } else {
+                        atomicAdd(&cnt[cr], cc);
+                        if (sum) atomicAdd(&sum[cr], csum);
+                        atomicMax(&pkey[cr], cb);
+                    }
+                }
+                const int last = 31 - __clz(heads);
+                if (rr != kNone && ((heads >> lane) & 1u) && lane != last) {
+                    atomicAdd(&cnt[rr], len);
+                    if (sum) atomicAdd(&sum[rr], sm);
+                    atomicMax(&pkey[rr], best);
+                }
+                cr = __shfl_sync(0xffffffffu, rr, last);
+                cc = __shfl_sync(0xffffffffu, len, last);
+                csum = __shfl_sync(0xffffffffu, sm, last);
+                cb = __shfl_sync(0xffffffffu, best, last);
+            }
+        }
+        if (lane == 0 && cr != kNone) {
+            atomicAdd(&cnt[cr], cc);
+            if (sum) atomicAdd(&sum[cr], csum);
+            atomicMax(&pkey[cr], cb);
         }
     }
 }
-
 // S5: the significance cut, in the same fp64 operations as the definition.
 // With f = 0 the cut is mean >= delta_s, which every set of members passes:
 // each member is >= delta_s, and rounding is monotone, so a running fp64
