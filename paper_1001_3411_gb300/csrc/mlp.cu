@@ -65,43 +65,139 @@ __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const floa
     }
 }
 
-// The learned first radius of every chunk in one pass: a warp computes the
-// 27 log-counts of 32 chunks into shared memory (one chunk at a time, 27
-// lanes looking up one stencil cell each), then each lane runs the network
-// for one of them: R = side * exp(MLP + margin).  Same arithmetic as the
-// feature kernel followed by mlp_fwd_kernel, without the features' round
-// trip through HBM.
-constexpr int kRadWarps = 4;
-__global__ void __launch_bounds__(kRadWarps * 32)
+// The learned first radius of every chunk in one pass, 32 chunks per warp:
+// each lane finds its chunk's stencil level and centre cell (the same
+// arithmetic as chunk_stencil), the warp looks up the 27 stencil cells of
+// one chunk at a time (27 lanes), and each lane runs the network for its
+// chunk with its activations in registers: R = side * exp(MLP + margin).
+// Weights sit in shared memory as fp32 values of the bf16 copy, laid out
+// so that a lane reads four consecutive outputs' weights at once.
+constexpr int kRadThreads = 128;
+constexpr int kRadWarps = kRadThreads / 32;
+constexpr int kFeatStride = IN + 2;   // 29: lane-strided feature rows hit distinct banks
+static_assert(H % 16 == 0, "hidden width in blocks of 16");
+
+struct RadWeights {
+    float w1t[IN][H];   // w1t[f][j] = W1[j][f]
+    float b1[H];
+    float w2t[H][H];    // w2t[i][o] = W2[o][i]
+    float b2[H];
+    float w3[H];
+    float b3;
+};
+
+__global__ void __launch_bounds__(kRadThreads, 4)
 radius_mlp_kernel(const __nv_bfloat16 *__restrict__ w16, const float4 *__restrict__ spos,
                   const uint64_t *__restrict__ keys, const uint32_t *__restrict__ cellT, int Ld,
                   int64_t n, int64_t n_chunks, int Q, float box, float inv_box,
                   const SegDesc *__restrict__ seg, int B, float margin, float *__restrict__ chunk_r)
 {
-    __shared__ float W[NP];
-    __shared__ float F[kRadWarps][32][IN + 1];
-    __shared__ float S[kRadWarps][32];
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) W[i] = bf(w16, i);
+    __shared__ __align__(16) RadWeights Ws;
+    __shared__ float F[kRadWarps][32][kFeatStride];
+    for (int i = threadIdx.x; i < H * IN; i += blockDim.x) Ws.w1t[i % IN][i / IN] = bf(w16, oW1 + i);
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) Ws.w2t[i % H][i / H] = bf(w16, oW2 + i);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        Ws.b1[i] = bf(w16, oB1 + i);
+        Ws.b2[i] = bf(w16, oB2 + i);
+        Ws.w3[i] = bf(w16, oW3 + i);
+    }
+    if (threadIdx.x == 0) Ws.b3 = bf(w16, oB3);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * kRadWarps * 32;
     for (int64_t base = ((int64_t)blockIdx.x * kRadWarps + w) * 32; base < n_chunks; base += stride) {
         const int nc = (int)min((int64_t)32, n_chunks - base);
+        // ---- the lane's chunk: stencil level, centre cell, cell side
+        const int64_t ch = base + (lane < nc ? lane : 0);
+        int64_t s0 = ch * Q, nend = n, cell0 = 0;
+        int ld = Ld;
+        float bx = box, ibx = inv_box;
+        if (seg) {
+            const SegDesc &d = seg[seg_of_chunk(seg, B, ch)];
+            s0 = d.base + (ch - d.chunk0) * Q;
+            nend = d.base + d.n;
+            cell0 = d.cell0;
+            ld = d.level_dense;
+            bx = (float)d.box;
+            ibx = (float)(1.0 / d.box);
+        }
+        const int nq = (int)min((int64_t)Q, nend - s0);
+        float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        for (int q = 0; q < nq; ++q) {
+            const float4 v = spos[s0 + q];
+            lx = fminf(lx, v.x);
+            ly = fminf(ly, v.y);
+            lz = fminf(lz, v.z);
+            hx = fmaxf(hx, v.x);
+            hy = fmaxf(hy, v.y);
+            hz = fmaxf(hz, v.z);
+        }
+        const float ext = fmaxf(hx - lx, fmaxf(hy - ly, hz - lz));
+        int l = kMaxLevel;
+        while (l > 2 && bx / (float)(1 << l) < ext) --l;
+        const int G = 1 << l;
+        const float sc = ibx * (float)G;
+        const int cx = min((int)floorf((lx + hx) * 0.5f * sc), G - 1);
+        const int cy = min((int)floorf((ly + hy) * 0.5f * sc), G - 1);
+        const int cz = min((int)floorf((lz + hz) * 0.5f * sc), G - 1);
+        const float side = (float)((double)bx / (double)G);
+        // ---- the 27 stencil counts of each chunk, one chunk at a time
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
         for (int j = 0; j < nc; ++j) {
-            uint32_t cnt, tot;
-            int l;
-            double side;
-            float rk;
-            chunk_stencil<float>(spos, keys, cellT, Ld, n, Q, box, inv_box, seg, B, base + j, nullptr, lane,
-                                 cnt, tot, l, side, rk);
-            if (lane < IN) F[w][j][lane] = log1pf((float)cnt);
-            if (lane == 0) S[w][j] = (float)side;
+            const int lj = __shfl_sync(0xffffffffu, l, j), ldj = __shfl_sync(0xffffffffu, ld, j);
+            const int xj = __shfl_sync(0xffffffffu, cx, j), yj = __shfl_sync(0xffffffffu, cy, j),
+                      zj = __shfl_sync(0xffffffffu, cz, j);
+            const int64_t c0 = __shfl_sync(0xffffffffu, cell0, j);
+            if (lane < IN) {
+                const int Gj = 1 << lj;
+                const int rx = (xj + dx + Gj) % Gj, ry = (yj + dy + Gj) % Gj, rz = (zj + dz + Gj) % Gj;
+                uint32_t a, b;
+                cell_range(cellT + c0, keys, ldj, lj, morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz), a, b);
+                F[w][j][lane] = log1pf((float)(b - a));
+            }
         }
         __syncwarp();
+        // ---- the network for the lane's chunk
         if (lane < nc) {
-            float h1[H];
-            const float y = mlp_forward_one(W, F[w][lane], h1);
-            chunk_r[base + lane] = S[w][lane] * expf(y + margin);
+            const float *x = F[w][lane];
+            float h[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) h[j] = Ws.b1[j];
+            for (int f = 0; f < IN; ++f) {
+                const float xf = x[f];
+                const float4 *r = (const float4 *)Ws.w1t[f];
+#pragma unroll
+                for (int j4 = 0; j4 < H / 4; ++j4) {
+                    const float4 wv = r[j4];
+                    h[4 * j4 + 0] = fmaf(wv.x, xf, h[4 * j4 + 0]);
+                    h[4 * j4 + 1] = fmaf(wv.y, xf, h[4 * j4 + 1]);
+                    h[4 * j4 + 2] = fmaf(wv.z, xf, h[4 * j4 + 2]);
+                    h[4 * j4 + 3] = fmaf(wv.w, xf, h[4 * j4 + 3]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < H; ++j) h[j] = fmaxf(h[j], 0.f);
+            float y = Ws.b3;
+            for (int ob = 0; ob < H; ob += 16) {
+                float acc[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) acc[m] = Ws.b2[ob + m];
+#pragma unroll
+                for (int i = 0; i < H; ++i) {
+                    const float4 *r = (const float4 *)&Ws.w2t[i][ob];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const float4 wv = r[k4];
+                        acc[4 * k4 + 0] = fmaf(wv.x, h[i], acc[4 * k4 + 0]);
+                        acc[4 * k4 + 1] = fmaf(wv.y, h[i], acc[4 * k4 + 1]);
+                        acc[4 * k4 + 2] = fmaf(wv.z, h[i], acc[4 * k4 + 2]);
+                        acc[4 * k4 + 3] = fmaf(wv.w, h[i], acc[4 * k4 + 3]);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 16; ++m) y = fmaf(Ws.w3[ob + m], fmaxf(acc[m], 0.f), y);
+            }
+            chunk_r[base + lane] = side * expf(y + margin);
         }
         __syncwarp();
     }
@@ -279,10 +375,10 @@ namespace {
 int radius_fused(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld,
                  int64_t n, int64_t n_chunks, int qpw, double box, const SegDesc *seg, int B, float *chunk_r)
 {
-    int64_t blocks = (n_chunks + kRadWarps * 32 - 1) / (kRadWarps * 32);
-    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 8);
+    int64_t blocks = (n_chunks + kRadThreads - 1) / kRadThreads;
+    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 4);
     blocks = std::max<int64_t>(blocks, 1);
-    radius_mlp_kernel<<<(unsigned)blocks, kRadWarps * 32, 0, c->stream>>>(
+    radius_mlp_kernel<<<(unsigned)blocks, kRadThreads, 0, c->stream>>>(
         (const __nv_bfloat16 *)c->mlp->w16, (const float4 *)spos, keys, cellT, Ld, n, n_chunks, qpw,
         (float)box, (float)(1.0 / box), seg, B, c->mlp->log_margin, chunk_r);
     HOP_LAUNCH(c);
