@@ -1093,6 +1093,24 @@ __device__ __forceinline__ void warp_sort32(unsigned long long &key, uint32_t &p
     }
 }
 
+// The same for a float key with a payload (equal keys in any order).
+__device__ __forceinline__ void warp_sort32_kv(float &key, uint32_t &pay, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(kAll, key, j);
+            const uint32_t op = __shfl_xor_sync(kAll, pay, j);
+            const bool take = (((lane & j) == 0) == ((lane & k) == 0)) ? o < key : o > key;
+            if (take) {
+                key = o;
+                pay = op;
+            }
+        }
+    }
+}
+
 // Exact rank-th smallest d^2 of the warp's list, whose entries in (lo, ...]
 // hold it with `below` smaller entries outside: up to 32 such entries (the
 // k-th bin) are sorted across the warp; more go through the radix descent.
@@ -1464,18 +1482,19 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                         no += __popc(bal);
                     }
                     __syncwarp();
-                    // sorted by (d^2, sorted index) first; equal distances, if
-                    // any, are sorted again by original index
-                    unsigned long long key = ~0ull;
+                    // sorted by d^2 first (a float key); equal distances, if
+                    // any, are sorted again by (d^2, original index)
+                    float fk = INFINITY;
                     uint32_t pay = 0u;
                     if (lane < no) {
                         pay = os[lane];
-                        key = ((unsigned long long)__float_as_uint(od[lane]) << 32) | pay;
+                        fk = od[lane];
                     }
-                    warp_sort32(key, pay, lane);
-                    const unsigned long long prev = __shfl_up_sync(kAll, key, 1);
-                    if (__any_sync(kAll, lane > 0 && lane < no && (prev >> 32) == (key >> 32))) {
-                        if (lane < no) key = (key & 0xffffffff00000000ull) | __float_as_uint(a.spos[pay].w);
+                    warp_sort32_kv(fk, pay, lane);
+                    const float prev = __shfl_up_sync(kAll, fk, 1);
+                    if (__any_sync(kAll, lane > 0 && lane < no && prev == fk)) {
+                        unsigned long long key = ~0ull;
+                        if (lane < no) key = ((unsigned long long)__float_as_uint(fk) << 32) | __float_as_uint(a.spos[pay].w);
                         warp_sort32(key, pay, lane);
                     }
                     if (lane < min(no, n_out)) a.nbr_s[(size_t)sq * a.ld_out + lane] = pay;
