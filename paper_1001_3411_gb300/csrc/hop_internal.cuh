@@ -146,19 +146,26 @@ int ctx_check_device_error(hop_ctx *c);            // syncs; maps the error word
     } while (0)
 
 // ------------------------------------------------------ device helpers ---
-__host__ __device__ inline uint64_t spread3_16(uint32_t v)
+
+// Morton code of cell (x, y, z), coordinates below 2^16: bit i of x, y and
+// z goes to bit 3i, 3i + 1 and 3i + 2.  The bits are spread on 8-bit halves
+// in 32-bit arithmetic: bits 0-7 of the coordinates fill bits 0-23 of the
+// code, bits 8-15 fill bits 24-47.
+__host__ __device__ inline uint32_t spread3_8(uint32_t v)
 {
-    uint64_t x = v & 0xFFFFu;
-    x = (x | (x << 16)) & 0x0000FF0000FFull;
-    x = (x | (x << 8)) & 0x00F00F00F00Full;
-    x = (x | (x << 4)) & 0x0C30C30C30C3ull;
-    x = (x | (x << 2)) & 0x249249249249ull;
-    return x;
+    v &= 0xFFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
 }
 
 __host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
 {
-    return spread3_16(x) | (spread3_16(y) << 1) | (spread3_16(z) << 2);
+    const uint32_t lo = spread3_8(x) | (spread3_8(y) << 1) | (spread3_8(z) << 2);
+    const uint32_t hi = spread3_8(x >> 8) | (spread3_8(y >> 8) << 1) | (spread3_8(z >> 8) << 2);
+    return ((uint64_t)hi << 24) | lo;
 }
 
 // Level of the dense cell table for n particles: the first level with at

@@ -859,27 +859,32 @@ struct WqSmem {
     }
 };
 
-// Bin of the rank-th entry over the histogram rows (lane b < kWqBins sums
-// bin b over the 32 lanes' columns):
-// the bin (-1 if fewer entries), the entries below it and up to it, and the
-// total.  Uniform over the warp.
-__device__ __forceinline__ void wq_rows_find(const int *hist, int lane, int rank, int &bin, int &below, int &upto,
-                                             int &tot)
+// Per-bin totals of the histogram rows (lane b < kWqBins: bin b, summed by
+// lanes b and b + 16 over half the columns each; column c of row b is read
+// at (c + b) mod 32, so every load hits 32 banks) and their inclusive prefix
+// over the lanes; tot = all counted entries.  Uniform over the warp.
+__device__ __forceinline__ void wq_rows_prefix(const int *hist, int lane, int &mine, int &incl, int &tot)
 {
-    int mine = 0;
-    // lane b reads column c of its row at (c + b) mod 32, so the lanes of
-    // each load hit different banks
-    if (lane < kWqBins) {
+    static_assert(kWqBins == 16, "two lanes per histogram row");
+    const int row = lane & 15, c0 = (lane >> 4) * 16;
+    int part = 0;
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) mine += hist[lane * 32 + ((r + lane) & 31)];
-    }
-    int incl = mine;
+    for (int r = 0; r < 16; ++r) part += hist[row * 32 + ((c0 + r + row) & 31)];
+    part += __shfl_xor_sync(kAll, part, 16);
+    mine = lane < kWqBins ? part : 0;
+    incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kAll, incl, o);
         if (lane >= o) incl += y;
     }
     tot = __shfl_sync(kAll, incl, 31);
+}
+
+// The bin holding the rank-th entry (-1 if fewer entries), the entries below
+// it and up to it, from the per-bin totals and prefix.
+__device__ __forceinline__ void wq_rows_rank(int mine, int incl, int rank, int &bin, int &below, int &upto)
+{
     const uint32_t hit = __ballot_sync(kAll, incl - mine < rank && rank <= incl);
     const int l = hit ? __ffs(hit) - 1 : 0;
     bin = hit ? l : -1;
@@ -1301,7 +1306,9 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                 }
                 __syncwarp();
                 int ntot;
-                wq_rows_find(hist, lane, k, bk, below_k, upto_k, ntot);
+                int rmine, rincl;
+                wq_rows_prefix(hist, lane, rmine, rincl, ntot);
+                wq_rows_rank(rmine, rincl, k, bk, below_k, upto_k);
                 if (!certified) {
                     if (ntot < k) {
                         ++retry_acc;
@@ -1317,8 +1324,8 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     certified = true;
                     bk0 = bk;
                     if (n_out > 0) {
-                        int b2, t2;
-                        wq_rows_find(hist, lane, n_out, bo, b2, upto_o, t2);
+                        int b2;
+                        wq_rows_rank(rmine, rincl, n_out, bo, b2, upto_o);
                         edge_o = bin_edge(top - (kWqBins - 1), shift, bo);
                     }
                 }
