@@ -951,14 +951,12 @@ __device__ int wq_cells(float qx, float qy, float qz, float r, float box, float 
 __device__ __forceinline__ uint32_t wq_prefix(const uint32_t *cln, uint32_t *cpre, int nc, int lane)
 {
     constexpr int PER = kWqCells / 32;
-    uint32_t v[PER];
-    uint32_t mine = 0;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int j = lane * PER + i;
-        v[i] = j < nc ? cln[j] : 0u;
-        mine += v[i];
-    }
+    static_assert(PER == 4, "one 16-byte read of cell lengths per lane");
+    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+    if (lane * PER < nc) q = reinterpret_cast<const uint4 *>(cln)[lane];
+    const uint32_t v[PER] = {nc > lane * PER ? q.x : 0u, nc > lane * PER + 1 ? q.y : 0u,
+                             nc > lane * PER + 2 ? q.z : 0u, nc > lane * PER + 3 ? q.w : 0u};
+    const uint32_t mine = v[0] + v[1] + v[2] + v[3];
     uint32_t incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1245,9 +1243,10 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                         __syncwarp();
                         nc = 1;
                     } else {
-                        l = 1;
-                        const float cells = box * (float)cpr / R;   // 2^l <= cells: side >= R / cpr
-                        while (l < kMaxLevel && (float)(1 << (l + 1)) <= cells) ++l;
+                        // the finest level with 2^l <= cells (side >= R / cpr), at
+                        // least 1: floor(log2(cells)) is the float's exponent
+                        const float cells = box * (float)cpr / R;
+                        l = min(max((int)((__float_as_uint(cells) >> 23) & 0xFFu) - 127, 1), kMaxLevel);
                         for (;;) {
                             nc = wq_cells(qx, qy, qz, R, box, inv_box, l, cellT, a.keys, level_dense, cra, cln, cmd,
                                           lane, lt);
@@ -1261,8 +1260,9 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     tauA = full ? INFINITY : R * R;
                     fresh = false;
                 }
-#pragma unroll 8
-                for (int b = 0; b < kWqBins; ++b) hist[b * 32 + lane] = 0;
+#pragma unroll
+                for (int i = 0; i < kWqBins * 32 / 128; ++i)   // the rows, four words per lane per store
+                    reinterpret_cast<int4 *>(hist)[i * 32 + lane] = make_int4(0, 0, 0, 0);
                 __syncwarp();
                 {
                     const int base = top - (kWqBins - 1);
