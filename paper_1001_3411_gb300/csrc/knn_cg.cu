@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 4) knn_cg_kernel(CgDev a)
 constexpr int kWqChunk = 4;                 // queries per chunk (the radius is per chunk)
 constexpr int kWqBins = 16;                 // histogram bins per lane row (quarter octaves of d^2)
 constexpr int kWqBinsLog = 4;
-constexpr int kWqGather = 256;              // entries the count scan keeps, so the gather scan can be skipped
+constexpr int kWqGather = 320;              // entries the count scan keeps, so the gather scan can be skipped
 constexpr int kWqCells = 128;               // cells of one query's region held at once
 
 // Shared memory of one warp, byte offsets.  The histogram rows (count
