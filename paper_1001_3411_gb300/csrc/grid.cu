@@ -262,8 +262,8 @@ int chunk_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint3
     if (p->pos_is_f64)
         return chunk_feat_launch<double>(c, spos, keys, cellT, Ld, n, p->box, qpw, p->n_dens,
                                          margin, chunk_r, nullptr, nullptr, nullptr, nullptr);
-    return chunk_feat_launch<float>(c, spos, keys, cellT, Ld, n, p->box, qpw, p->n_dens, margin,
-                                    chunk_r, nullptr, nullptr, nullptr, nullptr);
+    return radius_closed(c, spos, keys, cellT, Ld, n, (n + qpw - 1) / qpw, qpw, p->box, nullptr, 0, p->n_dens, margin,
+                         chunk_r);
 }
 
 // Features, levels and (if rk_s) targets for every chunk.
@@ -315,12 +315,5 @@ int grid_build_seg(hop_ctx *c, const float *pos, int64_t n, const SegDesc *seg, 
 int chunk_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
                      const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r)
 {
-    int64_t blocks = (n_chunks + 7) / 8;
-    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 16);
-    if (blocks < 1) blocks = 1;
-    chunk_feat_kernel<float><<<(unsigned)blocks, 256, 0, c->stream>>>(
-        (const float4 *)spos, keys, cellT, 0, 0, n_chunks, qpw, 1.f, 1.f, k, 0.25f, chunk_r, nullptr, nullptr,
-        nullptr, nullptr, seg, B);
-    HOP_LAUNCH(c);
-    return HOP_OK;
+    return radius_closed(c, spos, keys, cellT, 0, 0, n_chunks, qpw, 1.0, seg, B, k, 0.25f, chunk_r);
 }

@@ -377,6 +377,11 @@ int chunk_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const u
                      const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r);
 int mlp_radius_seg(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT,
                    const SegDesc *seg, int B, int64_t n_chunks, int qpw, int k, float *chunk_r);
+// mlp.cu: the closed-form first radius of every chunk (float32 positions),
+// from the same stencil counts as the learned one.
+int radius_closed(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld, int64_t n,
+                  int64_t n_chunks, int qpw, double box, const SegDesc *seg, int B, int k, float log_margin,
+                  float *chunk_r);
 
 // knn.cu
 struct KnnArgs {

@@ -1114,6 +1114,14 @@ __device__ __forceinline__ void warp_sort32_kv(float &key, uint32_t &pay, int la
     }
 }
 
+// The payloads of a warp sort by (d^2 bits, original index): the n_out list
+// when two distances are equal.  Out of line: it is rare.
+__device__ __noinline__ uint32_t wq_tie_sort(unsigned long long key, uint32_t pay, int lane)
+{
+    warp_sort32(key, pay, lane);
+    return pay;
+}
+
 // Exact rank-th smallest d^2 of the warp's list, whose entries in (lo, ...]
 // hold it with `below` smaller entries outside: up to 32 such entries (the
 // k-th bin) are sorted across the warp; more go through the radix descent.
@@ -1502,7 +1510,7 @@ __global__ void __launch_bounds__(kCgWarps * 32, 8) knn_wq_kernel(CgDev a)
                     if (__any_sync(kAll, lane > 0 && lane < no && prev == fk)) {
                         unsigned long long key = ~0ull;
                         if (lane < no) key = ((unsigned long long)__float_as_uint(fk) << 32) | __float_as_uint(a.spos[pay].w);
-                        warp_sort32(key, pay, lane);
+                        pay = wq_tie_sort(key, pay, lane);
                     }
                     if (lane < min(no, n_out)) a.nbr_s[(size_t)sq * a.ld_out + lane] = pay;
                 } else {

@@ -65,11 +65,15 @@ __global__ void mlp_fwd_kernel(const __nv_bfloat16 *__restrict__ w16, const floa
     }
 }
 
-// The learned first radius of every chunk in one pass, 32 chunks per warp:
-// each lane finds its chunk's stencil level and centre cell (the same
-// arithmetic as chunk_stencil), the warp looks up the 27 stencil cells of
-// one chunk at a time (27 lanes), and each lane runs the network for its
-// chunk with its activations in registers: R = side * exp(MLP + margin).
+// The first radius of every chunk in one pass, 32 chunks per warp: each
+// lane finds its chunk's stencil level and centre cell (the same arithmetic
+// as chunk_stencil), the warp looks up the 27 stencil cells of one chunk at
+// a time (27 lanes), and each lane turns its chunk's counts into a radius.
+// NET: the learned radius, R = side * exp(MLP + margin), the network run
+// with its activations in registers.  !NET: the closed form from the
+// stencil total, R = side * cbrt(81 k / (4 pi total)) * exp(margin), the
+// chunk's k-th-neighbour distance if the 27 cells held the mean density of
+// their total.
 // Weights sit in shared memory as fp32 values of the bf16 copy, laid out
 // so that a lane reads four consecutive outputs' weights at once.
 constexpr int kRadThreads = 128;
@@ -86,22 +90,26 @@ struct RadWeights {
     float b3;
 };
 
+template <bool NET>
 __global__ void __launch_bounds__(kRadThreads, 4)
-radius_mlp_kernel(const __nv_bfloat16 *__restrict__ w16, const float4 *__restrict__ spos,
-                  const uint64_t *__restrict__ keys, const uint32_t *__restrict__ cellT, int Ld,
-                  int64_t n, int64_t n_chunks, int Q, float box, float inv_box,
-                  const SegDesc *__restrict__ seg, int B, float margin, float *__restrict__ chunk_r)
+radius_kernel(const __nv_bfloat16 *__restrict__ w16, const float4 *__restrict__ spos,
+              const uint64_t *__restrict__ keys, const uint32_t *__restrict__ cellT, int Ld,
+              int64_t n, int64_t n_chunks, int Q, float box, float inv_box,
+              const SegDesc *__restrict__ seg, int B, float margin, int k, float *__restrict__ chunk_r)
 {
     __shared__ __align__(16) RadWeights Ws;
     __shared__ float F[kRadWarps][32][kFeatStride];
-    for (int i = threadIdx.x; i < H * IN; i += blockDim.x) Ws.w1t[i % IN][i / IN] = bf(w16, oW1 + i);
-    for (int i = threadIdx.x; i < H * H; i += blockDim.x) Ws.w2t[i % H][i / H] = bf(w16, oW2 + i);
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        Ws.b1[i] = bf(w16, oB1 + i);
-        Ws.b2[i] = bf(w16, oB2 + i);
-        Ws.w3[i] = bf(w16, oW3 + i);
+    __shared__ uint32_t T[kRadWarps][32];
+    if constexpr (NET) {
+        for (int i = threadIdx.x; i < H * IN; i += blockDim.x) Ws.w1t[i % IN][i / IN] = bf(w16, oW1 + i);
+        for (int i = threadIdx.x; i < H * H; i += blockDim.x) Ws.w2t[i % H][i / H] = bf(w16, oW2 + i);
+        for (int i = threadIdx.x; i < H; i += blockDim.x) {
+            Ws.b1[i] = bf(w16, oB1 + i);
+            Ws.b2[i] = bf(w16, oB2 + i);
+            Ws.w3[i] = bf(w16, oW3 + i);
+        }
+        if (threadIdx.x == 0) Ws.b3 = bf(w16, oB3);
     }
-    if (threadIdx.x == 0) Ws.b3 = bf(w16, oB3);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * kRadWarps * 32;
@@ -148,15 +156,29 @@ radius_mlp_kernel(const __nv_bfloat16 *__restrict__ w16, const float4 *__restric
             const int xj = __shfl_sync(0xffffffffu, cx, j), yj = __shfl_sync(0xffffffffu, cy, j),
                       zj = __shfl_sync(0xffffffffu, cz, j);
             const int64_t c0 = __shfl_sync(0xffffffffu, cell0, j);
+            uint32_t cnt = 0;
             if (lane < IN) {
                 const int Gj = 1 << lj;
                 const int rx = (xj + dx + Gj) % Gj, ry = (yj + dy + Gj) % Gj, rz = (zj + dz + Gj) % Gj;
                 uint32_t a, b;
                 cell_range(cellT + c0, keys, ldj, lj, morton3((uint32_t)rx, (uint32_t)ry, (uint32_t)rz), a, b);
-                F[w][j][lane] = log1pf((float)(b - a));
+                cnt = b - a;
+                if constexpr (NET) F[w][j][lane] = log1pf((float)cnt);
+            }
+            if constexpr (!NET) {
+                const uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0) T[w][j] = tot;
             }
         }
         __syncwarp();
+        if constexpr (!NET) {
+            if (lane < nc) {
+                const double r = (double)side * cbrt(81.0 * k / (4.0 * 3.14159265358979323846 * (double)max(T[w][lane], 1u)));
+                chunk_r[base + lane] = (float)(r * exp((double)margin));
+            }
+            __syncwarp();
+            continue;
+        }
         // ---- the network for the lane's chunk
         if (lane < nc) {
             const float *x = F[w][lane];
@@ -378,14 +400,29 @@ int radius_fused(hop_ctx *c, const void *spos, const uint64_t *keys, const uint3
     int64_t blocks = (n_chunks + kRadThreads - 1) / kRadThreads;
     blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 4);
     blocks = std::max<int64_t>(blocks, 1);
-    radius_mlp_kernel<<<(unsigned)blocks, kRadThreads, 0, c->stream>>>(
+    radius_kernel<true><<<(unsigned)blocks, kRadThreads, 0, c->stream>>>(
         (const __nv_bfloat16 *)c->mlp->w16, (const float4 *)spos, keys, cellT, Ld, n, n_chunks, qpw,
-        (float)box, (float)(1.0 / box), seg, B, c->mlp->log_margin, chunk_r);
+        (float)box, (float)(1.0 / box), seg, B, c->mlp->log_margin, 0, chunk_r);
     HOP_LAUNCH(c);
     return HOP_OK;
 }
 
 }  // namespace
+
+// The closed-form radius (float32 positions) with the same kernel.
+int radius_closed(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld, int64_t n,
+                  int64_t n_chunks, int qpw, double box, const SegDesc *seg, int B, int k, float log_margin,
+                  float *chunk_r)
+{
+    int64_t blocks = (n_chunks + kRadThreads - 1) / kRadThreads;
+    blocks = std::min<int64_t>(blocks, (int64_t)c->num_sms * 4);
+    blocks = std::max<int64_t>(blocks, 1);
+    radius_kernel<false><<<(unsigned)blocks, kRadThreads, 0, c->stream>>>(
+        nullptr, (const float4 *)spos, keys, cellT, Ld, n, n_chunks, qpw, (float)box, (float)(1.0 / box), seg, B,
+        log_margin, k, chunk_r);
+    HOP_LAUNCH(c);
+    return HOP_OK;
+}
 
 int mlp_radius(hop_ctx *c, const void *spos, const uint64_t *keys, const uint32_t *cellT, int Ld,
                int64_t n, const hop_params *p, int qpw, float *chunk_r)
