@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="override particle count (testing)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune-top", type=int, default=0,
+                    help="autotune over the first K candidates of each policy (0: all)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-subvolume section")
     ap.add_argument("--no-subhalos", action="store_true", help="skip the ADAPTAHOP subhalo section")
     # single-case mode: one box, a few passes, one JSON line of stage times
@@ -398,11 +400,12 @@ def run_gb300(args):
               "count": default_params(radius_mode=1)}
     # the autotuner (graph replays, untimed) picks each policy's tuning;
     # output does not depend on it
-    tuned = {}
+    tuned, tuned_from = {}, {}
     for name in ("learned", "count", "plain"):
-        cs = CANDS[name][:1] if args.no_tune else CANDS[name]
+        cs = CANDS[name][:1] if args.no_tune else (CANDS[name][:args.tune_top] if args.tune_top > 0 else CANDS[name])
         best, tr = hop.hop_autotune(dpos, off, boxes, params[name], cs, reps=1)
         tuned[name] = tuple(cs[best])
+        tuned_from[name] = [list(c) for c in cs]
 
     def configure(name):
         hop.apply_tuning(*tuned[name])
@@ -553,6 +556,7 @@ def run_gb300(args):
                    "l2": "inputs (12 B/particle, %.2f GB) larger than L2; no flush" % (n * 12 / 1e9),
                    "tuning": {k: {"queries_per_warp": v[0], "cells_per_radius": v[1], "buf_factor": v[2]}
                               for k, v in tuned.items()},
+                   "tuning_candidates": tuned_from,
                    "radius_model": model_src},
         "identical_output": bool(same),
         "n_groups": n_groups_ref,
