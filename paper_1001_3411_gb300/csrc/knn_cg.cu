@@ -1017,51 +1017,74 @@ __device__ __forceinline__ void wq_visit(const float4 *__restrict__ spos, const 
 // The n_out nearest of a warp's list when more than kOC entries lie up to
 // the n_out-th bin (long Nhop lists, ties): each entry up to edge_o is
 // ranked by (d^2, original index) against the whole list.  A lane ranks
-// four entries (e, e + 32, e + 64, e + 96) in one pass over the list;
-// equal distances are ordered by original index in a second pass, taken
-// only when some entry has one.  Out of line: the common path gathers at
-// most kOC entries instead.
+// four entries (e, e + 32, e + 64, e + 96) in one pass over the list.  The
+// first pass counts smaller distances only and writes the row; the ranks
+// of the m entries are then 0 .. m-1, summing to m(m-1)/2, unless two
+// distances are equal.  Only then does a second pass rank again by
+// (d^2, original index) and overwrite every position the first one wrote.
+// Out of line: the common path gathers at most kOC entries instead.
 __device__ __noinline__ void wq_rank_in_list(const float *Ld, const uint32_t *Ls, int cnt, float edge_o, int n_out,
                                              const float4 *__restrict__ spos, uint32_t *row, int lane)
 {
     constexpr int B = 4;
+    int m = 0, sum = 0;
     for (int e0 = 0; e0 < cnt; e0 += 32 * B) {
         float v[B];
-        int rank[B], eq[B];
+        int rank[B];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             const int e = e0 + 32 * j + lane;
             v[j] = e < cnt ? Ld[e] : INFINITY;
             if (!(v[j] <= edge_o)) v[j] = -1.f;   // not ranked; compares as nothing below it
             rank[j] = 0;
-            eq[j] = 0;
         }
         for (int f = 0; f < cnt; ++f) {
             const float u = Ld[f];
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                rank[j] += u < v[j];
-                eq[j] += u == v[j];
-            }
-        }
-        bool tie = false;
-#pragma unroll
-        for (int j = 0; j < B; ++j) tie |= v[j] >= 0.f && eq[j] > 1;
-        if (__any_sync(kAll, tie)) {
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const int e = e0 + 32 * j + lane;
-                if (!(v[j] >= 0.f && eq[j] > 1)) continue;
-                const uint32_t oe = __float_as_uint(spos[Ls[e]].w);
-                for (int f = 0; f < cnt; ++f)
-                    if (f != e && Ld[f] == v[j]) rank[j] += __float_as_uint(spos[Ls[f]].w) < oe;
-            }
+            for (int j = 0; j < B; ++j) rank[j] += u < v[j];
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            const int e = e0 + 32 * j + lane;
-            if (v[j] >= 0.f && rank[j] < n_out) row[rank[j]] = Ls[e];
+            if (!(v[j] >= 0.f)) continue;
+            ++m;
+            sum += rank[j];
+            if (rank[j] < n_out) row[rank[j]] = Ls[e0 + 32 * j + lane];
         }
+    }
+    m = (int)__reduce_add_sync(kAll, (unsigned)m);
+    sum = (int)__reduce_add_sync(kAll, (unsigned)sum);
+    if (sum == m * (m - 1) / 2) return;
+    __syncwarp();
+    for (int e0 = 0; e0 < cnt; e0 += 32 * B) {
+        float v[B];
+        int rank[B];
+        uint32_t oe[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int e = e0 + 32 * j + lane;
+            v[j] = e < cnt ? Ld[e] : INFINITY;
+            if (!(v[j] <= edge_o)) v[j] = -1.f;
+            rank[j] = 0;
+            oe[j] = v[j] >= 0.f ? __float_as_uint(spos[Ls[e]].w) : 0u;
+        }
+        for (int f = 0; f < cnt; ++f) {
+            const float u = Ld[f];
+            bool tie = false;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                rank[j] += u < v[j];
+                tie |= u == v[j];
+            }
+            if (tie) {
+                // the entry itself compares equal, never below
+                const uint32_t of = __float_as_uint(spos[Ls[f]].w);
+#pragma unroll
+                for (int j = 0; j < B; ++j) rank[j] += u == v[j] && of < oe[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (v[j] >= 0.f && rank[j] < n_out) row[rank[j]] = Ls[e0 + 32 * j + lane];
     }
 }
 
