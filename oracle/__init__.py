@@ -32,7 +32,14 @@ OK, EINVAL, ENOMEM, ECYCLE, ECAP = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle library (gcc -O2 -fopenmp); returns its path."""
+    """Compile the oracle library (gcc -O2 -fopenmp); returns its path.
+
+    ``HOP_ORACLE_LIB`` names another build of ``hop_oracle.c`` to load
+    instead: the mutation tests point it at copies compiled with one planted
+    mistake each, to show that the pins catch it."""
+    override = os.environ.get("HOP_ORACLE_LIB")
+    if override:
+        return override
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"

@@ -65,6 +65,31 @@ def test_symmetric_shell_has_its_centre_and_radius():
     assert rmax[0] == pytest.approx(rho, rel=1e-12)
 
 
+@pytest.mark.parametrize("axis,side", [(0, "low"), (0, "high"), (1, "low"), (1, "high")])
+def test_centre_wraps_when_the_peak_is_across_a_face(axis, side):
+    """A symmetric shell whose centre lies just inside one face while its
+    peak particle sits across it: the centre about the peak falls outside
+    [0, 1) before wrapping, and must come back to the shell's centre."""
+    rng = np.random.default_rng(8 + axis)
+    v = rng.normal(size=(150, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    c = np.array([0.5, 0.5, 0.5])
+    c[axis] = 0.998 if side == "low" else 0.002
+    rho = 0.006
+    pts = np.concatenate([c + rho * v, c - rho * v])
+    pos = np.mod(pts, 1.0)
+    # the peak: the member farthest across the face from the centre
+    k = int(np.argmax(pts[:, axis])) if side == "low" else int(np.argmin(pts[:, axis]))
+    assert (pts[k, axis] >= 1.0) if side == "low" else (pts[k, axis] < 0.0)
+    dens = np.ones(len(pos))
+    dens[k] = 2.0
+    count, peak, com, rmax = oracle.halo_stats(pos, dens, np.zeros(len(pos), dtype=np.int32), 1)
+    assert peak[0] == k
+    assert np.all((com[0] >= 0.0) & (com[0] < 1.0))
+    np.testing.assert_allclose(com[0], c, rtol=0, atol=1e-14)
+    assert rmax[0] == pytest.approx(rho, rel=1e-12)
+
+
 def test_each_group_equals_its_subset_alone_and_no_halo_is_skipped():
     rng = np.random.default_rng(6)
     pos = rng.random((3000, 3))

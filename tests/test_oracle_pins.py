@@ -256,6 +256,46 @@ def test_merge_fig1(variant):
     assert group[names.index("A")] == 0
 
 
+def test_merge_thresholds_are_inclusive():
+    """Sec. 3 ("Step By Step") calls chains with peak density >= delta_peak
+    proto-halos, and Sec. 2 merges proto-halos whose boundary density is
+    greater than or equal to delta_saddle: a peak exactly at delta_peak is
+    a halo, one just below it is not; a boundary exactly at delta_saddle
+    (s = 2 delta_saddle) merges two proto-halos."""
+    d_o, d_s, d_p = 80.0, 200.0, 240.0
+    below = np.nextafter(d_p, 0.0)
+    # chains 0 (peak exactly d_p), 1 (just below), 2 and 3 (proto-halos
+    # joined by a boundary exactly at the saddle threshold)
+    chain = np.array([0, 0, 1, 1, 2, 3], dtype=np.int32)
+    dens = np.array([d_p, 100.0, below, 100.0, 300.0, 250.0])
+    group, ng = oracle.merge(chain, dens, np.array([2], dtype=np.int32), np.array([3], dtype=np.int32),
+                             np.array([2.0 * d_s]), d_o, d_s, d_p)
+    assert ng == 2
+    assert group[4] == group[5] == 0            # merged; peak 300 numbered first
+    assert group[0] == group[1] == 1
+    assert group[2] == group[3] == -1
+    # the same boundary a hair below the threshold keeps them apart
+    group, ng = oracle.merge(chain, dens, np.array([2], dtype=np.int32), np.array([3], dtype=np.int32),
+                             np.array([np.nextafter(2.0 * d_s, 0.0)]), d_o, d_s, d_p)
+    assert ng == 3 and group[4] != group[5]
+
+
+def test_merge_equal_boundaries_follow_the_stated_order():
+    """The paper does not say which of two equal boundaries a sub-peak chain
+    follows.  The reading used here orders boundaries by (s descending, lo
+    ascending, hi ascending), lo < hi the chain labels: chain 3, with equal
+    boundaries to the separate proto-halos 0 and 1, joins 0 -- whichever
+    order the boundaries are listed in."""
+    chain = np.arange(4, dtype=np.int32)
+    dens = np.array([300.0, 260.0, 90.0, 150.0])       # 0, 1 proto-halos; 2 outside; 3 sub-peak
+    for order in ([0, 1], [1, 0]):
+        lo = np.array([[1, 0][i] for i in order], dtype=np.int32)
+        hi = np.array([3, 3], dtype=np.int32)
+        s = np.array([390.0, 390.0])
+        group, ng = oracle.merge(chain, dens, lo, hi, s, 80.0, 200.0, 240.0)
+        assert ng == 2 and group[3] == group[0] == 0 and group[1] == 1 and group[2] == -1
+
+
 def _msf_bruteforce(n_chain, proto, lo, hi, s, two_ds):
     """Exhaustive reference for C6: proto-halos joined by direct boundaries
     >= 2 delta_saddle form the owned sets; all owned sets are contracted to one
@@ -399,17 +439,23 @@ def test_plummer_isolated_spheres_give_one_halo_each():
 
 def test_mlp_oracle_hand_computed_case():
     """One active path through the network, computed by hand:
-    y = b3 + w3[0] * relu(b2[0] + W2[0,0] * relu(b1[0] + W1[0,2] * x2))."""
+    y = b3 + w3[0] * relu(b2[0] + W2[0,0] * relu(b1[0] + W1[0,2] * x2)),
+    plus a second-layer unit whose pre-activation -4 relu(...) is never
+    positive, so its ReLU keeps it out of y."""
     from oracle import mlp
     w1 = np.zeros((64, 27)); w1[0, 2] = 0.5
     b1 = np.zeros(64); b1[0] = -1.0
-    w2 = np.zeros((64, 64)); w2[0, 0] = 3.0
+    w2 = np.zeros((64, 64)); w2[0, 0] = 3.0; w2[1, 0] = -4.0
     b2 = np.zeros(64); b2[0] = 0.25
-    w3 = np.zeros(64); w3[0] = -2.0
+    w3 = np.zeros(64); w3[0] = -2.0; w3[1] = 1.0
     p = mlp.pack(w1, b1, w2, b2, w3, 0.75)
     x = np.zeros((3, 27)); x[:, 2] = [4.0, 1.0, 6.0]       # hidden pre-activations 1, -0.5, 2
     expect = [0.75 - 2.0 * (0.25 + 3.0 * 1.0), 0.75 - 2.0 * 0.25, 0.75 - 2.0 * (0.25 + 3.0 * 2.0)]
     np.testing.assert_allclose(mlp.forward(p, x), expect, rtol=0, atol=1e-14)
+    # the loss the gradient test differentiates is the mean squared error of these outputs
+    t = np.array([0.5, -1.0, 2.0])
+    loss, _ = mlp.loss_and_grad(p, x, t)
+    assert loss == pytest.approx(np.mean((np.array(expect) - t) ** 2), rel=1e-14)
 
 
 def test_mlp_oracle_gradient_matches_finite_differences():
