@@ -61,13 +61,13 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, pos, s, out):
+def _rank(rank, world, port, pos, s, out, params=None):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle_engine import OracleEngine
-        p = SimpleNamespace(**PARAMS)
+        p = SimpleNamespace(**(params or PARAMS))
         own = torch.nonzero(slab_of(torch.from_numpy(pos[:, 0]), 1.0, world) == rank).flatten()
         g, ng, info = parallel_hop(OracleEngine(), torch.from_numpy(pos[own.numpy()]), own, len(pos), p, s=s)
         gi = [None] * world
@@ -79,11 +79,11 @@ def _rank(rank, world, port, pos, s, out):
         dist.destroy_process_group()
 
 
-def _run(world, pos, s):
+def _run(world, pos, s, params=None):
     ctx = mp.get_context("spawn")
     q = ctx.SimpleQueue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, pos, s, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, pos, s, q, params)) for r in range(world)]
     for pr in procs:
         pr.start()
     res = q.get()
@@ -115,3 +115,37 @@ def test_decomposition_matches_single_process(world, s):
         assert max(info["rounds"] for *_, info in res) > 1
     # chains really cross the slab faces
     assert sum(info["published"] for *_, info in res) > 0
+
+
+def test_empty_slab_with_the_paper_defaults():
+    """The paper's own list lengths (Ndens = Nhop = 65, Nmerge = 4, Table 2)
+    on a box whose particles all lie in x < 0.6, so that the third of three
+    slabs owns none: its padding (Eq. 1 with N = 0) reaches the whole box,
+    so it receives every particle and labels none, and the other ranks'
+    groups still equal the single-process run's."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    rng = np.random.default_rng(11)
+    bg = rng.random((12000, 3)) * np.array([0.6, 1.0, 1.0])
+    parts = [bg]
+    for cx in (1.0 / 3.0, 0.5):
+        c = np.array([cx, rng.random(), rng.random()])
+        u = rng.uniform(0.0, 0.9, 1500)
+        r = 0.02 / np.sqrt(u ** (-2.0 / 3.0) - 1.0)
+        d = rng.normal(size=(1500, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        parts.append(c + r[:, None] * d)
+    pos = synth._wrap_f32(np.concatenate(parts), 1.0).astype(np.float64)
+    assert pos[:, 0].max() < 0.6
+    params = dict(PARAMS, n_dens=65, n_hop=65, n_merge=4)
+    ref = oracle.hop(pos, **params)
+    res = _run(3, pos, 1.5, params)
+    group = np.full(len(pos), -2, dtype=np.int32)
+    for own, g, ng, info in res:
+        group[own] = g
+        assert ng == ref["n_groups"]
+    # the empty slab owns nothing and is padded with every other particle
+    assert len(res[2][0]) == 0 and res[2][3]["padded"] == len(pos)
+    assert np.all(group != -2)
+    assert np.array_equal(group, ref["group"])
+    assert ref["n_groups"] >= 2
