@@ -257,11 +257,12 @@ def test_merge_fig1(variant):
 
 
 def test_merge_thresholds_are_inclusive():
-    """Sec. 3 ("Step By Step") calls chains with peak density >= delta_peak
-    proto-halos, and Sec. 2 merges proto-halos whose boundary density is
-    greater than or equal to delta_saddle: a peak exactly at delta_peak is
-    a halo, one just below it is not; a boundary exactly at delta_saddle
-    (s = 2 delta_saddle) merges two proto-halos."""
+    """Both thresholds are inclusive (Sec. 3, "Step By Step", writes the
+    proto-halo test as peak >= delta_peak and the saddle test as
+    delta_link >= delta_saddle; Sec. 2 states the saddle test the same
+    way): a peak exactly at delta_peak is a halo, one just below it is not;
+    a boundary exactly at delta_saddle (s = 2 delta_saddle) merges two
+    proto-halos."""
     d_o, d_s, d_p = 80.0, 200.0, 240.0
     below = np.nextafter(d_p, 0.0)
     # chains 0 (peak exactly d_p), 1 (just below), 2 and 3 (proto-halos
