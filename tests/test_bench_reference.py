@@ -1,5 +1,6 @@
 """The benchmark's reference arm (the oracle on the host cores) on a small
-box: one JSON line with the contract's keys, run as the driver runs it."""
+box: one JSON line with the contract's keys, from the same command line as a
+full run (`bench.py --impl reference`)."""
 import json
 import os
 import subprocess
