@@ -45,6 +45,8 @@ MUTANTS = [
     ("self excluded from the sum", "orc_density", "for (int32_t t = 0; t < k; ++t)", "for (int32_t t = 1; t < k; ++t)"),
     ("kernel normalisation h^2", "orc_density", "(M_PI * h * h * h)", "(M_PI * h * h)"),
     ("kernel normalisation without pi", "orc_density", "(M_PI * h * h * h)", "(h * h * h)"),
+    ("kernel argument d^2 / h", "orc_density", "m4_w(sqrt(row[t]) / h)", "m4_w(row[t] / h)"),
+    ("smoothing length from the (k-1)-th entry", "orc_density", "sqrt(row[k - 1])", "sqrt(row[k - 2])"),
     # C3, C4 link
     ("hop over Nhop - 1 entries", "orc_link", "t < n_hop; ++t", "t < n_hop - 1; ++t"),
     ("hop skips the particle itself", "orc_link", "int32_t best = row[0];", "int32_t best = row[1];"),
@@ -58,6 +60,8 @@ MUTANTS = [
      "raw[w].s = dens[i] < dens[j] ? dens[i] : dens[j];"),
     ("boundary keeps the smallest sum", "link_cmp", "return a->s > b->s ? -1 : 1;", "return a->s < b->s ? -1 : 1;"),
     ("boundaries over Nmerge - 1 entries", "orc_boundaries", "t < n_merge; ++t", "t < n_merge - 1; ++t"),
+    ("boundaries keyed by particles", "orc_boundaries", "int32_t a = chain[i], b = chain[j];",
+     "int32_t a = (int32_t)i, b = j;"),
     # C6, C7 merge
     ("proto-halo test strict", "orc_merge", "dens[peak[c]] >= d_peak", "dens[peak[c]] > d_peak"),
     ("proto-halo test on delta_saddle", "orc_merge", "dens[peak[c]] >= d_peak", "dens[peak[c]] >= d_saddle"),
@@ -67,6 +71,9 @@ MUTANTS = [
      "if (a == b) continue;"),
     ("edges taken in ascending order", "edge_cmp", "return a->s > b->s ? -1 : 1;", "return a->s < b->s ? -1 : 1;"),
     ("equal edges ordered by hi first", "edge_cmp", "if (a->lo != b->lo) return a->lo < b->lo ? -1 : 1;", ""),
+    ("chain peak is its first member", "orc_merge",
+     "if (peak[c] < 0 || key_greater(dens, (int32_t)i, peak[c])) peak[c] = (int32_t)i;",
+     "if (peak[c] < 0) peak[c] = (int32_t)i;"),
     ("delta_outer cut dropped", "orc_merge", "(dens[i] >= d_outer && owned[r])", "(owned[r])"),
     ("groups numbered by ascending peak", "peak_cmp", "return a->d > b->d ? -1 : 1;", "return a->d < b->d ? -1 : 1;"),
     # C8 halo statistics
@@ -77,11 +84,16 @@ MUTANTS = [
      "sum[3 * g + d] += pos[3 * i + d] - pos[3 * (int64_t)peak[g] + d];"),
     ("radius from the peak", "orc_halo_stats", "min_image(pos[3 * i + d] - com[3 * g + d], box)",
      "min_image(pos[3 * i + d] - pos[3 * (int64_t)peak[g] + d], box)"),
+    ("halo peak is its first member", "orc_halo_stats",
+     "if (peak[g] < 0 || key_greater(dens, (int32_t)i, peak[g])) peak[g] = (int32_t)i;",
+     "if (peak[g] < 0) peak[g] = (int32_t)i;"),
     ("centre divided by count + 1", "orc_halo_stats", "/ (double)count[g]", "/ (double)(count[g] + 1)"),
     # C9 subhalos
     ("symmetric pairs emitted twice", "orc_sym_boundaries", "if (raw[t].a > raw[t].b) continue;", ""),
     ("one-way links kept", "orc_sym_boundaries", "if (l == d || raw[l].a != raw[t].b || raw[l].b != raw[t].a) continue;",
      "if (l < d && raw[l].a == raw[t].b && raw[l].b == raw[t].a) { }"),
+    ("symmetric value from one direction", "orc_sym_boundaries",
+     "s[u] = raw[t].s > raw[l].s ? raw[t].s : raw[l].s;", "s[u] = raw[t].s;"),
     ("subhalo links cut without the factor 2", "orc_subhalos", "s[e] >= 2.0 * ds", "s[e] >= ds"),
     ("subhalo members below the threshold", "orc_subhalos", "out[i] = dens[i] >= ds ?", "out[i] = dens[i] >= 0.0 ?"),
     ("Poisson noise 1/N", "orc_subhalos", "f_poisson / sqrt(N)", "f_poisson / N"),

@@ -265,21 +265,21 @@ def test_merge_thresholds_are_inclusive():
     proto-halos."""
     d_o, d_s, d_p = 80.0, 200.0, 240.0
     below = np.nextafter(d_p, 0.0)
-    # chains 0 (peak exactly d_p, with members exactly at and just below
-    # delta_outer), 1 (peak just below d_p), 2 and 3 (proto-halos joined by
-    # a boundary exactly at the saddle threshold)
-    chain = np.array([0, 0, 1, 1, 2, 3, 0, 0], dtype=np.int32)
-    dens = np.array([d_p, 100.0, below, 100.0, 300.0, 250.0, d_o, np.nextafter(d_o, 0.0)])
-    group, ng = oracle.merge(chain, dens, np.array([2], dtype=np.int32), np.array([3], dtype=np.int32),
-                             np.array([2.0 * d_s]), d_o, d_s, d_p)
+    # chain 1: peak (particle 1) exactly at d_p, with members exactly at and
+    # just below delta_outer; chain 3: peak just below d_p; chains 4 and 5:
+    # proto-halos joined by a boundary exactly at the saddle threshold.
+    # Chains are labelled by their peak, which is not their first member.
+    chain = np.array([1, 1, 3, 3, 4, 5, 1, 1], dtype=np.int32)
+    dens = np.array([100.0, d_p, 100.0, below, 300.0, 250.0, d_o, np.nextafter(d_o, 0.0)])
+    edge = (np.array([4], dtype=np.int32), np.array([5], dtype=np.int32))
+    group, ng = oracle.merge(chain, dens, *edge, np.array([2.0 * d_s]), d_o, d_s, d_p)
     assert ng == 2
     assert group[4] == group[5] == 0            # merged; peak 300 numbered first
     assert group[0] == group[1] == group[6] == 1
     assert group[7] == -1                       # below delta_outer: in no halo (Sec. 2)
     assert group[2] == group[3] == -1
     # the same boundary a hair below the threshold keeps them apart
-    group, ng = oracle.merge(chain, dens, np.array([2], dtype=np.int32), np.array([3], dtype=np.int32),
-                             np.array([np.nextafter(2.0 * d_s, 0.0)]), d_o, d_s, d_p)
+    group, ng = oracle.merge(chain, dens, *edge, np.array([np.nextafter(2.0 * d_s, 0.0)]), d_o, d_s, d_p)
     assert ng == 3 and group[4] != group[5]
 
 
