@@ -1,7 +1,8 @@
 """Host-side logic of the benchmark that needs no GPU: the provenance check
 that decides whether the committed ncu traffic figure still describes the
 kNN kernel, the clock-sample summary that accepts or rejects a timed run,
-and the GPU index a rank takes from CUDA_VISIBLE_DEVICES."""
+the GPU index a rank takes from CUDA_VISIBLE_DEVICES, and that every
+command the profile summaries give is one this benchmark accepts."""
 import json
 import os
 import re
@@ -103,3 +104,25 @@ def test_gpu_index_follows_visible_devices(monkeypatch):
     assert bench.gpu_index(1) == 1                  # a UUID: the rank's ordinal
     monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
     assert bench.gpu_index(3) == 3
+
+
+def test_profile_commands_are_accepted_by_the_benchmark(monkeypatch):
+    """Each profile summary names the command that produced it; every
+    `python bench.py ...` line there (also the one ncu wraps) must parse
+    with the benchmark's own arguments."""
+    import glob
+    import shlex
+    import sys
+    prof = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert prof
+    seen = 0
+    for path in prof:
+        text = open(path).read().replace("\\\n", " ")
+        cmds = re.findall(r"python bench\.py[^\n`]*", text)
+        assert cmds, f"{os.path.basename(path)} gives no bench.py command"
+        for c in cmds:
+            argv = shlex.split(c)[1:]
+            monkeypatch.setattr(sys, "argv", argv)
+            bench.parse()
+            seen += 1
+    assert seen >= len(prof)
